@@ -1,0 +1,191 @@
+/*
+ * rtr.h - C ABI of the GB300 randomized tensor-ring decomposition library.
+ *
+ * Method: Yuan, Li, Cao, Zhao, "Randomized Tensor Ring Decomposition and Its
+ * Application to Large-scale Data Reconstruction" (arXiv:1901.01652),
+ * Algorithm 1 (rTRD), Eq. 1-4.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status (RTR_OK = 0).  On failure
+ *    rtr_last_error() returns a message for the calling host thread.
+ *  - Tensors are dense, row-major, last mode fastest.  dims[] has N entries,
+ *    3 <= N <= 8 for the decomposition entry points (rtr_reconstruct also
+ *    accepts N = 2).  Mode numbers are 0-based (the paper counts from 1).
+ *  - TR cores are float64, core n of shape R_n x I_n x R_{n+1} row-major,
+ *    with R_{N+1} = R_1 (Section 2.2).
+ *  - All data pointers are DEVICE pointers owned by the caller; arrays of
+ *    pointers (double* const* Y, ...) are HOST arrays of N device pointers.
+ *    The library allocates device memory only in rtr_plan_create (its
+ *    workspace and tables) and frees it in rtr_plan_destroy.
+ *  - Every compute call takes a cudaStream_t (passed as void*; NULL = the
+ *    legacy default stream), is asynchronous on that stream and does not
+ *    synchronise.  Calls on one plan must not overlap in time (the plan's
+ *    workspace is shared by its calls); use one plan per concurrent stream.
+ *  - Input-dependent numerical events (non-finite values, a Cholesky that
+ *    fell back) are recorded in device flags that rtr_plan_flags() reads.
+ */
+#ifndef RTR_H
+#define RTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RTR_OK            0
+#define RTR_EINVAL        1   /* bad argument (null pointer, size, rank, precision) */
+#define RTR_ENOMEM        2   /* workspace allocation failed */
+#define RTR_ECUDA         3   /* a CUDA call failed (message has the CUDA error) */
+#define RTR_ENONFINITE    4   /* non-finite values met (device flag) */
+#define RTR_ENOTCONV      5   /* warning: a fallback path was taken; results written */
+#define RTR_ETIMEOUT      6   /* a bounded device wait gave up (device flag) */
+#define RTR_EUNSUPPORTED  7   /* valid request this build does not implement */
+
+/* arithmetic of the sketch and mode-product chain (Algorithm 1, steps 5, 7) */
+#define RTR_FP64  0   /* X float64; every step float64                            */
+#define RTR_FP32  1   /* X float32; SIMT float32 sketch / chain, float64 QR & solves */
+#define RTR_BF16  2   /* X float32; tcgen05 BF16 (hi+lo split) sketch / chain      */
+
+/* device flag bits (rtr_plan_flags) */
+#define RTR_FLAG_NONFINITE     1   /* NaN/Inf met in an input or a reduction */
+#define RTR_FLAG_QR_FALLBACK   2   /* CholeskyQR2 failed; Householder QR used */
+#define RTR_FLAG_GRAM_PINV     4   /* an ALS Gram matrix was not SPD; pseudo-inverse used */
+#define RTR_FLAG_TIMEOUT       8   /* a bounded device wait gave up */
+
+typedef struct rtr_plan rtr_plan;
+
+typedef struct {
+    int      prec;            /* RTR_FP64 / RTR_FP32 / RTR_BF16 */
+    uint64_t seed;            /* seed of the Gaussian test matrices Omega_n */
+    int      sweeps;          /* TR-ALS sweeps (each updates cores 1..N once) */
+    double   tol;             /* TR-SVD relative tolerance epsilon */
+    int      flags;           /* reserved, 0 */
+    int      chain_order[8];  /* order of the mode products of step 7; all -1 = default
+                                 (largest I_n/K_n first, ties to the later mode) */
+} rtr_params;
+
+/* Fill *p with defaults: FP32, seed 0, 20 sweeps, tol 1e-2, default chain order. */
+void rtr_params_default(rtr_params* p);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* rtr_last_error(void);
+
+/*
+ * Create a plan for an order-N tensor of shape dims[N] with projection sizes
+ * K[N] (Algorithm 1, input [K_n]) and TR ranks R[N] (input R_1..R_N).
+ * A mode with K_n >= I_n is not projected: Q_n = I and K_n := I_n (the
+ * paper keeps such a mode whole in Section 4.1).  Limits: 1 <= K_n <= 64
+ * for projected modes, 1 <= R_n <= 16.  Allocates the workspace on the
+ * current device.  The plan is owned by the caller; free with rtr_plan_destroy.
+ */
+int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K,
+                    const int* R, const rtr_params* params);
+int rtr_plan_destroy(rtr_plan* plan);
+
+/* Effective K_n (after the K_n >= I_n rule) and the chain order the plan uses. */
+int rtr_plan_info(const rtr_plan* plan, int* K_eff, int* chain_order);
+
+/* Read and clear the device flags (synchronises the device). */
+int rtr_plan_flags(rtr_plan* plan, int* flags);
+
+/*
+ * Algorithm 1, steps 4-5: for every projected mode n,
+ *     Y_n = X_(n) Omega_n        (I_n x K_n, float64, row-major)
+ * X: dims, float64 for RTR_FP64 plans, float32 otherwise.  Omega_n is never
+ * stored: entry (r, k) is generated in the kernel from Philox4x64-10 with key
+ * (seed, n) and counter (r, k/20, 0, 0) mapped through the 4096-level Gaussian
+ * quantile table (float64 values for RTR_FP64, bfloat16-rounded values for
+ * RTR_FP32 and RTR_BF16); r is the row-major index of the other modes.
+ * Y[n] may be NULL for modes that are not projected.  Also records ||X||_F^2
+ * in the plan for rtr_rse.
+ */
+int rtr_sketch(rtr_plan* plan, const void* X, double* const* Y, void* stream);
+
+/*
+ * Algorithm 1, steps 6-7 (Eq. 3): Q_n = orth(Y_n) (economy QR with diag(R) > 0,
+ * CholeskyQR2 in float64, Householder fallback), then
+ *     P = X x_{pi_1} Q_{pi_1}^T ... x_{pi_N} Q_{pi_N}^T
+ * in the plan's chain order.  Y[n]: I_n x K_n float64 (ignored for modes that
+ * are not projected).  Q[n]: I_n x K_n float64 output (identity written for
+ * unprojected modes).  P: K_1 x ... x K_N output, float64 for RTR_FP64 plans,
+ * float32 otherwise.  X is read once by the first product; later products read
+ * the plan's intermediates.
+ */
+int rtr_project(rtr_plan* plan, const void* X, const double* const* Y,
+                double* const* Q, void* P, void* stream);
+
+/*
+ * Algorithm 1, step 9 with TR-ALS: fit cores Z_n (R_n x K_n x R_{n+1},
+ * float64) to P by `sweeps` sweeps of exact least-squares core updates
+ * (Eq. 2: P_<n> = Z_{n,(2)} S^T, S the subchain; Z_{n,(2)} = P_<n> S (S^T S)^-1,
+ * the Gram S^T S formed from float64 transfer matrices and solved in float64).
+ * Z: in/out.  If init_given != 0 the Z buffers hold the starting cores;
+ * otherwise the library writes its default start (discrete-Gaussian cores
+ * from Philox4x64-10 with key (seed + 1, 256 + n), scaled so ||TR(Z)|| = ||P||).
+ * err: device float64[sweeps] (may be NULL) receives ||P - TR(Z)||_F after
+ * each sweep.
+ */
+int rtr_als(rtr_plan* plan, const void* P, double* const* Z, int init_given,
+            double* err, void* stream);
+
+/*
+ * Algorithm 1, step 9 with TR-SVD (Section 4.1 tolerance): sequential
+ * truncated SVDs of P with delta = tol ||P|| / sqrt(N) (sqrt(2) delta for the
+ * first, whose rank is split R_1 R_2 with R_1 the largest divisor <= sqrt).
+ * ranks: host int[N]; if ranks[0] > 0 on entry the ranks are forced, else they
+ * are chosen and written back.  Z: device buffers, each of capacity
+ * R_max(n) x K_n x R_max(n+1) float64 with the plan's R as capacity.
+ * (Returns RTR_EUNSUPPORTED in builds without the TR-SVD kernels.)
+ */
+int rtr_svd(rtr_plan* plan, const void* P, double tol, double* const* Z,
+            int* ranks, void* stream);
+
+/*
+ * Algorithm 1, step 11 (read as the mode-2 product of the order-3 core):
+ *     G_n = Z_n x_2 Q_n,   G_n[a, i, b] = sum_k Z_n[a, k, b] Q_n[i, k]
+ * Z[n]: R_n x K_n x R_{n+1}; Q[n]: I_n x K_n; G[n]: R_n x I_n x R_{n+1}; all float64.
+ * ranks: host int[N] ranks of Z (NULL = the plan's R).
+ */
+int rtr_backproject(rtr_plan* plan, const double* const* Z, const double* const* Q,
+                    double* const* G, const int* ranks, void* stream);
+
+/*
+ * Psi([G_n]) of Eq. 4: the dense tensor of a TR (Eq. 1),
+ *     Xhat(i_1..i_N) = Trace(G_1(i_1) ... G_N(i_N)).
+ * N >= 2; G[n]: R[n] x dims[n] x R[(n+1)%N] float64.  out_prec RTR_FP64 writes
+ * float64, RTR_FP32 writes float32 (accumulated in float32).  Allocates
+ * nothing: the caller passes `work` (device, at least rtr_reconstruct_work_bytes
+ * bytes).  No plan needed.
+ */
+size_t rtr_reconstruct_work_bytes(int N, const int64_t* dims, const int* R);
+int rtr_reconstruct(int N, const int64_t* dims, const int* R, const double* const* G,
+                    int out_prec, void* Xhat, void* work, size_t work_bytes, void* stream);
+
+/*
+ * RSE of Section 4 without forming the large tensor:
+ *     ||X - Psi(G)||^2 = ||X||^2 - ||P||^2 + ||P - TR(Z)||^2
+ * (Eq. 3 with orthonormal Q_n).  ||X||^2 is the value recorded by the plan's
+ * last rtr_sketch; P and Z as given to rtr_als / rtr_svd (ranks NULL = plan R).
+ * out: device float64[1].
+ */
+int rtr_rse(rtr_plan* plan, const void* P, const double* const* Z, const int* ranks,
+            double* out, void* stream);
+
+/*
+ * Test support: write rows row0..row0+nrows-1 of Omega_n (K columns, float64
+ * values of the table the plan's precision uses) to out (device, nrows x K).
+ */
+int rtr_draw_omega(rtr_plan* plan, int mode, int64_t row0, int64_t nrows, int K,
+                   double* out, void* stream);
+
+/* Test support: the Gaussian table of a precision as float64 values (host out[4096]). */
+int rtr_gaussian_table(int prec, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTR_H */

@@ -1,0 +1,148 @@
+// Block-level float64 dense kernels on shared-memory matrices (one CTA).
+#pragma once
+#include "rtr_internal.cuh"
+
+namespace rtr {
+
+// In-place lower Cholesky G = L L^T of an n x n SPD matrix (row-major, ld,
+// n <= 256).  Returns false (uniformly across the block) if a pivot is not
+// finite or not above rel_tol times the original diagonal entry (rel_tol = 0
+// is the LAPACK potrf failure condition, pivot <= 0).
+__device__ inline bool block_cholesky(double* G, int n, int ld, double rel_tol = 0.0) {
+    __shared__ int fail;
+    __shared__ double diag0[256];
+    if (threadIdx.x == 0) fail = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) diag0[k] = G[k * ld + k];
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = G[k * ld + k];
+            if (!(d > rel_tol * diag0[k]) || !(d > 0.0) || !isfinite(d)) fail = 1;
+            else G[k * ld + k] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) return false;
+        const double piv = G[k * ld + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) G[i * ld + k] /= piv;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+            if (j <= i) G[i * ld + j] -= G[i * ld + k] * G[j * ld + k];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// One warp solves L L^T z = w in place (w of length n in shared or global
+// memory, stride 1), L lower from block_cholesky.  Column-oriented sweeps.
+__device__ inline void warp_chol_solve(const double* L, int n, int ld, double* w) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < n; ++k) {             // forward: L y = w
+        const double yk = w[k] / L[k * ld + k];
+        __syncwarp();
+        if (lane == 0) w[k] = yk;
+        for (int l = k + 1 + lane; l < n; l += 32) w[l] -= L[l * ld + k] * yk;
+        __syncwarp();
+    }
+    for (int k = n - 1; k >= 0; --k) {        // backward: L^T z = y
+        const double zk = w[k] / L[k * ld + k];
+        __syncwarp();
+        if (lane == 0) w[k] = zk;
+        for (int l = lane; l < k; l += 32) w[l] -= L[k * ld + l] * zk;
+        __syncwarp();
+    }
+}
+
+__device__ inline double block_sum(double v, double* red /* >= 32 doubles */) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// Cyclic Jacobi eigendecomposition of a symmetric n x n matrix A (row-major,
+// ld) in shared memory, parallel round-robin pairing (n/2 disjoint rotations
+// per step).  On return the diagonal of A holds the eigenvalues and the
+// columns of V (n x n, ld) the eigenvectors.  `pairs` needs 2*((n+1)/2) ints,
+// `cs` needs 2*((n+1)/2) doubles.
+__device__ inline void block_jacobi_eig(double* A, double* V, int n, int ld, int* pairs, double* cs,
+                                        int max_sweeps) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
+    __syncthreads();
+    if (n < 2) return;
+    const int m = (n + 1) & ~1;             // even player count (dummy = n when odd)
+    const int np = m / 2;
+    __shared__ double off_s, tot_s;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        // convergence test: off-diagonal mass relative to the whole
+        if (tid == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const double a = A[i * ld + j];
+                    tot += a * a;
+                    if (i != j) off += a * a;
+                }
+            off_s = off; tot_s = tot;
+        }
+        __syncthreads();
+        if (!(off_s > 1e-30 * tot_s)) break;
+        for (int step = 0; step < m - 1; ++step) {
+            // round-robin pairing: player 0 fixed, others rotate
+            for (int k = tid; k < np; k += nt) {
+                int p = (k == 0) ? 0 : 1 + (k - 1 + step) % (m - 1);
+                int q = 1 + (m - 2 - k + step) % (m - 1);
+                if (p > q) { const int t = p; p = q; q = t; }
+                pairs[2 * k] = p; pairs[2 * k + 1] = q;
+                double c = 1.0, sn = 0.0;
+                if (q < n) {
+                    const double apq = A[p * ld + q];
+                    if (apq != 0.0) {
+                        const double app = A[p * ld + p], aqq = A[q * ld + q];
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = t * c;
+                    }
+                }
+                cs[2 * k] = c; cs[2 * k + 1] = sn;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int e = tid; e < np * n; e += nt) {
+                const int k = e / n, j = e % n;
+                const int p = pairs[2 * k], q = pairs[2 * k + 1];
+                if (q >= n) continue;
+                const double c = cs[2 * k], sn = cs[2 * k + 1];
+                const double ap = A[p * ld + j], aq = A[q * ld + j];
+                A[p * ld + j] = c * ap - sn * aq;
+                A[q * ld + j] = sn * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int e = tid; e < np * n; e += nt) {
+                const int k = e / n, i = e % n;
+                const int p = pairs[2 * k], q = pairs[2 * k + 1];
+                if (q >= n) continue;
+                const double c = cs[2 * k], sn = cs[2 * k + 1];
+                const double ap = A[i * ld + p], aq = A[i * ld + q];
+                A[i * ld + p] = c * ap - sn * aq;
+                A[i * ld + q] = sn * ap + c * aq;
+                const double vp = V[i * ld + p], vq = V[i * ld + q];
+                V[i * ld + p] = c * vp - sn * vq;
+                V[i * ld + q] = sn * vp + c * vq;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace rtr

@@ -1,0 +1,406 @@
+// C ABI of the rTRD library: plans, workspace, Gaussian tables, dispatch of
+// Algorithm 1's steps to the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include "rtr_internal.cuh"
+
+size_t contract_partial_elems(int num_sms, int64_t I, int C);
+size_t contract_norm_elems(int num_sms, int64_t I, int C);
+size_t orth_ws_elems(int num_sms, int64_t maxI);
+int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s);
+int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
+                  cudaStream_t s);
+size_t tc_ws_bytes(const rtr_plan* p);
+
+namespace {
+thread_local char g_err[1024] = "";
+
+// ---- Gaussian quantile table (library's own copy) ------------------------------
+// T[j] = Phi^{-1}((j + 1/2) / 4096): lower half by bisection on
+// Phi(x) = erfc(-x / sqrt 2) / 2 (accurate in relative terms for x < 0) with
+// a Newton polish, upper half by the symmetry of N(0, 1).
+double phi_lower(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+double inv_phi_lower(double p) {
+    double lo = -40.0, hi = 0.0;
+    for (int it = 0; it < 2000; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (phi_lower(mid) < p) lo = mid; else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 2; ++it) {
+        const double f = phi_lower(x) - p;
+        const double d = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+        x -= f / d;
+    }
+    return x;
+}
+
+void gaussian_table64(double* t) {
+    for (int j = 0; j < 2048; ++j) {
+        const double v = inv_phi_lower((j + 0.5) / 4096.0);
+        t[j] = v;
+        t[4095 - j] = -v;
+    }
+}
+
+// round a double to 8 significant bits, ties to even, as a bfloat16 pattern
+uint16_t bf16_bits(double x) {
+    if (x == 0.0) return std::signbit(x) ? 0x8000 : 0;
+    int e;
+    const double m = std::frexp(x, &e);               // |m| in [0.5, 1)
+    const double r = std::ldexp(std::nearbyint(std::ldexp(m, 8)), e - 8);
+    const float f = (float)r;                          // exact
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+int choose_order(rtr_plan* p) {
+    const rtr_params& pr = p->params;
+    bool given = true;
+    for (int n = 0; n < p->N; ++n) if (pr.chain_order[n] < 0) given = false;
+    if (given) {
+        int seen[RTR_MAXN] = {};
+        for (int n = 0; n < p->N; ++n) {
+            const int m = pr.chain_order[n];
+            if (m >= p->N || seen[m]) return rtr_set_error(RTR_EINVAL, "chain_order is not a permutation");
+            seen[m] = 1;
+            p->order[n] = m;
+        }
+        return RTR_OK;
+    }
+    // largest shrink first (smallest K_n / I_n), ties to the later mode
+    int idx[RTR_MAXN];
+    for (int n = 0; n < p->N; ++n) idx[n] = n;
+    std::stable_sort(idx, idx + p->N, [&](int a, int b) {
+        const double ra = (double)p->K[a] / (double)p->dims[a], rb = (double)p->K[b] / (double)p->dims[b];
+        if (ra != rb) return ra < rb;
+        return a > b;
+    });
+    for (int n = 0; n < p->N; ++n) p->order[n] = idx[n];
+    return RTR_OK;
+}
+
+void free_plan(rtr_plan* p) {
+    if (!p) return;
+    cudaFree(p->tab64); cudaFree(p->tab32); cudaFree(p->tab_bf16);
+    cudaFree(p->partial); cudaFree(p->normx_part); cudaFree(p->scal);
+    cudaFree(p->chain[0]); cudaFree(p->chain[1]);
+    cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
+    cudaFree(p->flags); cudaFree(p->tc_ws);
+    delete p;
+}
+
+template <typename T>
+int dalloc(T** ptr, size_t elems) {
+    cudaError_t e = cudaMalloc((void**)ptr, std::max<size_t>(elems, 1) * sizeof(T));
+    if (e != cudaSuccess) { cudaGetLastError(); return rtr_set_error(RTR_ENOMEM, "cudaMalloc(%zu B) failed: %s", elems * sizeof(T), cudaGetErrorString(e)); }
+    return RTR_OK;
+}
+}  // namespace
+
+int rtr_set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+int rtr_cuda_check(cudaError_t e, const char* what) {
+    return rtr_set_error(RTR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" {
+
+const char* rtr_last_error(void) { return g_err; }
+
+void rtr_params_default(rtr_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->prec = RTR_FP32;
+    p->seed = 0;
+    p->sweeps = 20;
+    p->tol = 1e-2;
+    for (int n = 0; n < 8; ++n) p->chain_order[n] = -1;
+}
+
+int rtr_gaussian_table(int prec, double* out) {
+    if (!out) return rtr_set_error(RTR_EINVAL, "out is NULL");
+    double t[4096];
+    gaussian_table64(t);
+    for (int j = 0; j < 4096; ++j) {
+        if (prec == RTR_FP64) out[j] = t[j];
+        else if (prec == RTR_FP32 || prec == RTR_BF16) out[j] = (double)bf16_value(bf16_bits(t[j]));
+        else return rtr_set_error(RTR_EINVAL, "unknown precision %d", prec);
+    }
+    return RTR_OK;
+}
+
+int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, const int* R,
+                    const rtr_params* params) {
+    if (!plan || !dims || !K || !R || !params) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    *plan = nullptr;
+    if (N < 3 || N > RTR_MAXN) return rtr_set_error(RTR_EINVAL, "order N=%d outside [3, 8]", N);
+    if (params->prec != RTR_FP64 && params->prec != RTR_FP32 && params->prec != RTR_BF16)
+        return rtr_set_error(RTR_EINVAL, "unknown precision %d", params->prec);
+    if (params->sweeps < 0) return rtr_set_error(RTR_EINVAL, "sweeps < 0");
+    rtr_plan* p = new (std::nothrow) rtr_plan();
+    if (!p) return rtr_set_error(RTR_ENOMEM, "host allocation failed");
+    p->N = N;
+    p->params = *params;
+    p->numel = 1;
+    p->pnumel = 1;
+    for (int n = 0; n < N; ++n) {
+        if (dims[n] < 1) { delete p; return rtr_set_error(RTR_EINVAL, "dims[%d] = %lld < 1", n, (long long)dims[n]); }
+        if (K[n] < 1) { delete p; return rtr_set_error(RTR_EINVAL, "K[%d] = %d < 1", n, K[n]); }
+        if (R[n] < 1 || R[n] > RTR_MAX_RANK) { delete p; return rtr_set_error(RTR_EINVAL, "R[%d] = %d outside [1, 16]", n, R[n]); }
+        p->dims[n] = dims[n];
+        p->Kreq[n] = K[n];
+        p->proj[n] = (int64_t)K[n] < dims[n];
+        p->K[n] = p->proj[n] ? K[n] : (int)std::min<int64_t>(dims[n], 1 << 30);
+        if (p->proj[n] && K[n] > RTR_MAX_KSKETCH) { delete p; return rtr_set_error(RTR_EINVAL, "K[%d] = %d > 64", n, K[n]); }
+        if (!p->proj[n] && dims[n] > 4096) { delete p; return rtr_set_error(RTR_EINVAL, "unprojected mode %d longer than 4096", n); }
+        p->R[n] = R[n];
+        p->numel *= dims[n];
+        p->pnumel *= p->K[n];
+    }
+    int st = choose_order(p);
+    if (st) { delete p; return st; }
+    cudaError_t ce = cudaGetDevice(&p->device);
+    if (ce != cudaSuccess) { delete p; return rtr_cuda_check(ce, "cudaGetDevice"); }
+    ce = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (ce != cudaSuccess) { delete p; return rtr_cuda_check(ce, "cudaDeviceGetAttribute"); }
+    const bool f64 = params->prec == RTR_FP64;
+    const size_t esz = f64 ? 8 : 4;
+
+    // ---- workspace sizes
+    size_t part = 1024, normp = 1024;
+    int64_t maxI = 1, maxJ = 1;
+    int maxR = 1;
+    for (int n = 0; n < N; ++n) {
+        maxR = std::max(maxR, R[n]);
+        if (p->proj[n]) {
+            part = std::max(part, contract_partial_elems(p->num_sms, dims[n], p->K[n]));
+            normp = std::max(normp, contract_norm_elems(p->num_sms, dims[n], p->K[n]));
+            maxI = std::max<int64_t>(maxI, dims[n]);
+        }
+        const int C = R[n] * R[(n + 1) % N];
+        part = std::max(part, contract_partial_elems(p->num_sms, p->K[n], C));
+        maxJ = std::max<int64_t>(maxJ, p->pnumel / p->K[n]);
+    }
+    // chain intermediates (ping-pong); the last product goes straight to P
+    int64_t cdims[RTR_MAXN];
+    for (int n = 0; n < N; ++n) cdims[n] = dims[n];
+    int nsteps = 0;
+    for (int s = 0; s < N; ++s) if (p->proj[p->order[s]]) ++nsteps;
+    size_t chain_elems[2] = {0, 0};
+    int step = 0;
+    for (int s = 0; s < N; ++s) {
+        const int n = p->order[s];
+        if (!p->proj[n]) continue;
+        cdims[n] = p->K[n];
+        int64_t sz = 1;
+        for (int m = 0; m < N; ++m) sz *= cdims[m];
+        if (step < nsteps - 1) chain_elems[step & 1] = std::max<size_t>(chain_elems[step & 1], (size_t)sz);
+        ++step;
+    }
+    size_t chain_bytes0 = std::max(chain_elems[0] * esz, (size_t)p->pnumel * 8);
+    size_t chain_bytes1 = chain_elems[1] * esz;
+    // subchain buffers (>= J x R^2 per level) and reconstruct work for rtr_rse
+    size_t sub_bytes = esz * (size_t)maxJ * (size_t)(maxR * maxR);
+    int64_t kd[RTR_MAXN];
+    for (int n = 0; n < N; ++n) kd[n] = p->K[n];
+    sub_bytes = std::max(sub_bytes, (reconstruct_work_bytes(N, kd, R) + 1) / 2);
+    sub_bytes = (sub_bytes + 255) & ~(size_t)255;
+
+    // ---- allocations
+    double t64[4096];
+    gaussian_table64(t64);
+    float t32[4096];
+    uint16_t tb[4096];
+    for (int j = 0; j < 4096; ++j) { tb[j] = bf16_bits(t64[j]); t32[j] = bf16_value(tb[j]); }
+#define RTR_TRY(x) do { int s_ = (x); if (s_) { free_plan(p); return s_; } } while (0)
+#define RTR_TRYC(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { free_plan(p); return rtr_cuda_check(e_, #x); } } while (0)
+    RTR_TRY(dalloc(&p->tab64, 4096));
+    RTR_TRY(dalloc(&p->tab32, 4096));
+    RTR_TRY(dalloc(&p->tab_bf16, 4096));
+    RTR_TRYC(cudaMemcpy(p->tab64, t64, sizeof(t64), cudaMemcpyHostToDevice));
+    RTR_TRYC(cudaMemcpy(p->tab32, t32, sizeof(t32), cudaMemcpyHostToDevice));
+    RTR_TRYC(cudaMemcpy(p->tab_bf16, tb, sizeof(tb), cudaMemcpyHostToDevice));
+    RTR_TRY(dalloc(&p->partial, part)); p->partial_elems = part;
+    RTR_TRY(dalloc(&p->normx_part, normp)); p->normx_part_elems = normp;
+    RTR_TRY(dalloc(&p->scal, 64));
+    RTR_TRYC(cudaMemset(p->scal, 0, 64 * sizeof(double)));
+    {
+        char* c0 = nullptr;
+        char* c1 = nullptr;
+        RTR_TRY(dalloc(&c0, chain_bytes0)); p->chain[0] = c0; p->chain_bytes[0] = chain_bytes0;
+        RTR_TRY(dalloc(&c1, std::max<size_t>(chain_bytes1, 256))); p->chain[1] = c1; p->chain_bytes[1] = chain_bytes1;
+    }
+    p->qr_ws_elems = orth_ws_elems(p->num_sms, maxI);
+    RTR_TRY(dalloc(&p->qr_ws, p->qr_ws_elems));
+    p->als_wmax = 0;
+    for (int n = 0; n < N; ++n)
+        p->als_wmax = std::max<size_t>(p->als_wmax, (size_t)p->K[n] * R[n] * R[(n + 1) % N]);
+    p->als_ws_elems = (size_t)(RTR_MAXN + 2) * 256 * 256 + 2 * p->als_wmax + 2 * 144 * 144;
+    RTR_TRY(dalloc(&p->als_ws, p->als_ws_elems));
+    {
+        char* sb = nullptr;
+        RTR_TRY(dalloc(&sb, 2 * sub_bytes));
+        p->sub_ws[0] = sb; p->sub_ws[1] = sb + sub_bytes; p->sub_bytes = sub_bytes;
+    }
+    RTR_TRY(dalloc(&p->flags, 4));
+    RTR_TRYC(cudaMemset(p->flags, 0, 4 * sizeof(int)));
+    p->tc_ws_bytes = tc_ws_bytes(p);
+    if (p->tc_ws_bytes) {
+        char* t = nullptr;
+        RTR_TRY(dalloc(&t, p->tc_ws_bytes));
+        p->tc_ws = t;
+    }
+#undef RTR_TRY
+#undef RTR_TRYC
+    *plan = p;
+    return RTR_OK;
+}
+
+int rtr_plan_destroy(rtr_plan* plan) {
+    free_plan(plan);
+    return RTR_OK;
+}
+
+int rtr_plan_info(const rtr_plan* p, int* K_eff, int* chain_order) {
+    if (!p) return rtr_set_error(RTR_EINVAL, "plan is NULL");
+    for (int n = 0; n < p->N; ++n) {
+        if (K_eff) K_eff[n] = p->K[n];
+        if (chain_order) chain_order[n] = p->order[n];
+    }
+    return RTR_OK;
+}
+
+int rtr_plan_flags(rtr_plan* p, int* flags) {
+    if (!p || !flags) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    RTR_CUDA(cudaDeviceSynchronize());
+    RTR_CUDA(cudaMemcpy(flags, p->flags, sizeof(int), cudaMemcpyDeviceToHost));
+    RTR_CUDA(cudaMemset(p->flags, 0, sizeof(int)));
+    return RTR_OK;
+}
+
+int rtr_sketch(rtr_plan* p, const void* X, double* const* Y, void* stream) {
+    if (!p || !X || !Y) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int n = 0; n < p->N; ++n)
+        if (p->proj[n] && !Y[n]) return rtr_set_error(RTR_EINVAL, "Y[%d] is NULL", n);
+    if (p->params.prec == RTR_BF16) return launch_sketch_tc(p, (const float*)X, Y, s);
+    const int f64 = p->params.prec == RTR_FP64;
+    bool norm_done = false;
+    for (int n = 0; n < p->N; ++n) {
+        if (!p->proj[n]) continue;
+        ContractArgs a{};
+        int64_t A, I, B;
+        rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
+        a.X = X; a.A = A; a.I = I; a.B = B; a.C = p->K[n];
+        a.gen = 1; a.seed = p->params.seed; a.mode = n;
+        a.table = f64 ? (const void*)p->tab64 : (const void*)p->tab32;
+        a.Y = Y[n];
+        a.norm_out = norm_done ? nullptr : p->scal + 0;
+        int st = launch_contract(p, f64, a, s);
+        if (st) return st;
+        norm_done = true;
+    }
+    if (!norm_done) return launch_sumsq(X, f64, p->numel, p->partial, 1024, p->scal + 0, s);
+    return RTR_OK;
+}
+
+int rtr_project(rtr_plan* p, const void* X, const double* const* Y, double* const* Q, void* P, void* stream) {
+    if (!p || !X || !Y || !Q || !P) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = launch_orth(p, Y, Q, s);
+    if (st) return st;
+    const int f64 = p->params.prec == RTR_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    int64_t cd[RTR_MAXN];
+    for (int n = 0; n < p->N; ++n) cd[n] = p->dims[n];
+    int nsteps = 0;
+    for (int i = 0; i < p->N; ++i) if (p->proj[p->order[i]]) ++nsteps;
+    if (nsteps == 0) {
+        RTR_CUDA(cudaMemcpyAsync(P, X, (size_t)p->numel * esz, cudaMemcpyDeviceToDevice, s));
+        return RTR_OK;
+    }
+    const void* cur = X;
+    int step = 0;
+    for (int i = 0; i < p->N; ++i) {
+        const int n = p->order[i];
+        if (!p->proj[n]) continue;
+        int64_t A, I, B;
+        rtr_mode_view(p->N, cd, n, &A, &I, &B);
+        void* out = (step == nsteps - 1) ? P : p->chain[step & 1];
+        if (p->params.prec == RTR_BF16 && step == 0)
+            st = launch_ttm_tc(p, (const float*)cur, A, I, B, Q[n], p->K[n], (float*)out, s);
+        else
+            st = launch_ttm(p, f64, cur, A, I, B, Q[n], p->K[n], out, s);
+        if (st) return st;
+        cd[n] = p->K[n];
+        cur = out;
+        ++step;
+    }
+    return RTR_OK;
+}
+
+int rtr_als(rtr_plan* p, const void* P, double* const* Z, int init_given, double* err, void* stream) {
+    if (!p || !P || !Z) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    for (int n = 0; n < p->N; ++n) if (!Z[n]) return rtr_set_error(RTR_EINVAL, "Z[%d] is NULL", n);
+    return run_als(p, P, Z, init_given, err, (cudaStream_t)stream);
+}
+
+int rtr_svd(rtr_plan* p, const void* P, double tol, double* const* Z, int* ranks, void* stream) {
+    if (!p || !P || !Z || !ranks) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    return run_trsvd(p, P, tol, Z, ranks, (cudaStream_t)stream);
+}
+
+int rtr_backproject(rtr_plan* p, const double* const* Z, const double* const* Q, double* const* G, const int* ranks,
+                    void* stream) {
+    if (!p || !Z || !Q || !G) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    return run_backproject(p, Z, Q, G, ranks, (cudaStream_t)stream);
+}
+
+size_t rtr_reconstruct_work_bytes(int N, const int64_t* dims, const int* R) {
+    if (N < 2 || N > RTR_MAXN || !dims || !R) return 0;
+    return reconstruct_work_bytes(N, dims, R);
+}
+
+int rtr_reconstruct(int N, const int64_t* dims, const int* R, const double* const* G, int out_prec, void* Xhat,
+                    void* work, size_t work_bytes, void* stream) {
+    if (N < 2 || N > RTR_MAXN) return rtr_set_error(RTR_EINVAL, "order N=%d outside [2, 8]", N);
+    if (!dims || !R || !G || !Xhat || !work) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    for (int n = 0; n < N; ++n) {
+        if (!G[n]) return rtr_set_error(RTR_EINVAL, "G[%d] is NULL", n);
+        if (dims[n] < 1 || R[n] < 1 || R[n] > RTR_MAX_RANK) return rtr_set_error(RTR_EINVAL, "bad dims/R at mode %d", n);
+    }
+    if (out_prec != RTR_FP64 && out_prec != RTR_FP32) return rtr_set_error(RTR_EINVAL, "out_prec must be FP64 or FP32");
+    return run_reconstruct(N, dims, R, G, out_prec, Xhat, work, work_bytes, (cudaStream_t)stream);
+}
+
+int rtr_rse(rtr_plan* p, const void* P, const double* const* Z, const int* ranks, double* out, void* stream) {
+    if (!p || !P || !Z || !out) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    return run_rse(p, P, Z, ranks, out, (cudaStream_t)stream);
+}
+
+int rtr_draw_omega(rtr_plan* p, int mode, int64_t row0, int64_t nrows, int K, double* out, void* stream) {
+    if (!p || !out) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    if (mode < 0 || mode >= p->N || row0 < 0 || nrows < 0 || K < 1) return rtr_set_error(RTR_EINVAL, "bad range");
+    return run_draw_omega(p, mode, row0, nrows, K, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

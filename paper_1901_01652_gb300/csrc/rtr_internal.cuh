@@ -1,0 +1,147 @@
+// Internal declarations of the rTRD CUDA library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "rtr.h"
+
+#define RTR_MAXN 8
+#define RTR_MAX_KSKETCH 64
+#define RTR_MAX_RANK 16
+
+struct rtr_plan {
+    int N = 0;
+    int64_t dims[RTR_MAXN] = {};
+    int Kreq[RTR_MAXN] = {};
+    int K[RTR_MAXN] = {};        // effective projection size
+    int R[RTR_MAXN] = {};
+    int proj[RTR_MAXN] = {};     // 1 if mode is projected (K < I)
+    int order[RTR_MAXN] = {};    // chain order
+    rtr_params params{};
+    int device = 0;
+    int num_sms = 0;
+    int64_t numel = 0;           // |X|
+    int64_t pnumel = 0;          // |P|
+
+    // device Gaussian tables (4096 entries)
+    double* tab64 = nullptr;     // float64 quantiles
+    float* tab32 = nullptr;      // bfloat16-rounded quantiles as float
+    uint16_t* tab_bf16 = nullptr;// bfloat16 bit patterns
+
+    // workspace
+    double* partial = nullptr;   size_t partial_elems = 0;    // split-K partials
+    double* normx_part = nullptr; size_t normx_part_elems = 0;
+    double* scal = nullptr;      // scalars: [0] ||X||^2 [1] ||P||^2 [2..] misc
+    void* chain[2] = {nullptr, nullptr}; size_t chain_bytes[2] = {0, 0};
+    double* qr_ws = nullptr;     size_t qr_ws_elems = 0;      // orth workspace
+    double* als_ws = nullptr;    size_t als_ws_elems = 0;     // FP64 ALS workspace
+    size_t als_wmax = 0;         // max K_n R_n R_{n+1}
+    void* sub_ws[2] = {nullptr, nullptr}; size_t sub_bytes = 0;  // subchain ping-pong
+    int* flags = nullptr;
+    void* tc_ws = nullptr;       size_t tc_ws_bytes = 0;       // tensor-core path workspace
+};
+
+// ---- error reporting (rtr_api.cu) -------------------------------------------
+int rtr_set_error(int code, const char* fmt, ...);
+int rtr_cuda_check(cudaError_t e, const char* what);
+#define RTR_CUDA(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return rtr_cuda_check(e_, #call); } while (0)
+#define RTR_LAUNCH_CHECK(what) do { cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return rtr_cuda_check(e_, what); } while (0)
+
+static inline int64_t rtr_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// mode view (A, I, B) of a shape
+static inline void rtr_mode_view(int N, const int64_t* dims, int n, int64_t* A, int64_t* I, int64_t* B) {
+    int64_t a = 1, b = 1;
+    for (int m = 0; m < n; ++m) a *= dims[m];
+    for (int m = n + 1; m < N; ++m) b *= dims[m];
+    *A = a; *I = dims[n]; *B = b;
+}
+
+// ---- launchers implemented in the kernel translation units -------------------
+// k_sketch.cu: generic split-K "mode contraction"
+//   Y[i, c] = sum_{a,b} X[a, i, b] * M[r(a,b), c]     (i < I, c < C)
+// with M either generated (Gaussian test matrix Omega_n, r = a*B + b) or read
+// from memory (row r = a*B + b, leading dimension ldm).  Writes FP64 partials
+// and reduces them deterministically into Y (ldy = C).
+struct ContractArgs {
+    const void* X; int64_t A; int64_t I; int64_t B;
+    int C;
+    // generated operand
+    int gen; uint64_t seed; int mode; const void* table;
+    // stored operand (gen == 0), same element type as X
+    const void* M; int64_t ldm;
+    double* Y;                  // I x C float64 output
+    double* norm_out;           // optional: receives sum x^2 (float64) of X
+};
+int launch_contract(rtr_plan* p, int is_f64, const ContractArgs& a, cudaStream_t s);
+
+// k_ttm.cu: out[a, k, b] = sum_i X[a, i, b] * Q[i, k]   (Q: I x K float64)
+int launch_ttm(rtr_plan* p, int is_f64, const void* X, int64_t A, int64_t I, int64_t B,
+               const double* Q, int K, void* out, cudaStream_t s);
+
+// k_linalg.cu
+int launch_orth(rtr_plan* p, const double* const* Y, double* const* Q, cudaStream_t s);
+int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out,
+                 cudaStream_t s);
+
+// k_als.cu
+int run_als(rtr_plan* p, const void* P, double* const* Z, int init_given, double* err,
+            cudaStream_t s);
+int run_backproject(rtr_plan* p, const double* const* Z, const double* const* Q,
+                    double* const* G, const int* ranks, cudaStream_t s);
+int run_reconstruct(int N, const int64_t* dims, const int* R, const double* const* G,
+                    int out_prec, void* Xhat, void* work, size_t work_bytes, cudaStream_t s);
+size_t reconstruct_work_bytes(int N, const int64_t* dims, const int* R);
+int run_rse(rtr_plan* p, const void* P, const double* const* Z, const int* ranks, double* out,
+            cudaStream_t s);
+int run_draw_omega(rtr_plan* p, int mode, int64_t row0, int64_t nrows, int K, double* out,
+                   cudaStream_t s);
+
+// k_trsvd.cu
+int run_trsvd(rtr_plan* p, const void* P, double tol, double* const* Z, int* ranks, cudaStream_t s);
+
+// ---- device helpers ----------------------------------------------------------
+#ifdef __CUDACC__
+namespace rtr {
+
+// Philox4x64-10 (Salmon et al., SC'11): 256-bit counter, 128-bit key.
+__device__ __forceinline__ void philox4x64_10(uint64_t& c0, uint64_t& c1, uint64_t& c2, uint64_t& c3,
+                                              uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; k1 += W1; }
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+}
+
+// The 20 table indices of one Philox call for Omega_n row r, column block cb:
+// index t (0..19) is bits 12*(t%5).. of word t/5.
+__device__ __forceinline__ void omega_words(uint64_t seed, int mode, uint64_t r, uint64_t cb,
+                                            uint64_t w[4]) {
+    uint64_t c0 = r, c1 = cb, c2 = 0, c3 = 0;
+    philox4x64_10(c0, c1, c2, c3, seed, (uint64_t)mode);
+    w[0] = c0; w[1] = c1; w[2] = c2; w[3] = c3;
+}
+__device__ __forceinline__ int omega_field(const uint64_t w[4], int t) {
+    return (int)((w[t / 5] >> (12 * (t % 5))) & 0xFFFull);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace rtr
+#endif

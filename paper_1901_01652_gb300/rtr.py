@@ -1,0 +1,250 @@
+"""Python binding of librtr.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls
+(``include/rtr.h``), takes torch CUDA tensors for device buffers, and does no
+arithmetic of its own.  If the compiled library is missing, ``lib()`` raises:
+there is no CPU or PyTorch fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librtr.so")
+
+RTR_OK, RTR_EINVAL, RTR_ENOMEM, RTR_ECUDA, RTR_ENONFINITE, RTR_ENOTCONV, RTR_ETIMEOUT, RTR_EUNSUPPORTED = range(8)
+RTR_FP64, RTR_FP32, RTR_BF16 = 0, 1, 2
+PREC = {"fp64": RTR_FP64, "fp32": RTR_FP32, "bf16": RTR_BF16}
+FLAG_NONFINITE, FLAG_QR_FALLBACK, FLAG_GRAM_PINV, FLAG_TIMEOUT = 1, 2, 4, 8
+
+# every entry point of include/rtr.h
+ENTRY_POINTS = (
+    "rtr_params_default", "rtr_last_error", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
+    "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_als", "rtr_svd", "rtr_backproject",
+    "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
+)
+
+
+class RtrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rtr status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("sweeps", ctypes.c_int),
+                ("tol", ctypes.c_double), ("flags", ctypes.c_int), ("chain_order", ctypes.c_int * 8)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_VPP = ctypes.POINTER(ctypes.c_void_p)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    """Load librtr.so (built by ``paper_1901_01652_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_1901_01652_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "rtr_params_default": (None, [ctypes.POINTER(Params)]),
+        "rtr_last_error": (ctypes.c_char_p, []),
+        "rtr_plan_create": (ctypes.c_int, [_VPP, ctypes.c_int, _I64P, _IP, _IP, ctypes.POINTER(Params)]),
+        "rtr_plan_destroy": (ctypes.c_int, [_VP]),
+        "rtr_plan_info": (ctypes.c_int, [_VP, _IP, _IP]),
+        "rtr_plan_flags": (ctypes.c_int, [_VP, _IP]),
+        "rtr_sketch": (ctypes.c_int, [_VP, _VP, _VPP, _VP]),
+        "rtr_project": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
+        "rtr_als": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.c_int, _VP, _VP]),
+        "rtr_svd": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VPP, _IP, _VP]),
+        "rtr_backproject": (ctypes.c_int, [_VP, _VPP, _VPP, _VPP, _IP, _VP]),
+        "rtr_reconstruct_work_bytes": (ctypes.c_size_t, [ctypes.c_int, _I64P, _IP]),
+        "rtr_reconstruct": (ctypes.c_int, [ctypes.c_int, _I64P, _IP, _VPP, ctypes.c_int, _VP, _VP,
+                                           ctypes.c_size_t, _VP]),
+        "rtr_rse": (ctypes.c_int, [_VP, _VP, _VPP, _IP, _VP, _VP]),
+        "rtr_draw_omega": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _VP, _VP]),
+        "rtr_gaussian_table": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != RTR_OK:
+        raise RtrError(status, lib().rtr_last_error().decode())
+
+
+def _dev(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t
+
+
+def _ptr(t):
+    return _VP(0 if t is None else t.data_ptr())
+
+
+def _ptrs(ts, dtype=None, name="buffers"):
+    arr = (_VP * len(ts))()
+    for i, t in enumerate(ts):
+        _dev(t, dtype, f"{name}[{i}]")
+        arr[i] = 0 if t is None else t.data_ptr()
+    return arr
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _VP(s.cuda_stream)
+
+
+def _i64(xs):
+    return (ctypes.c_int64 * len(xs))(*[int(x) for x in xs])
+
+
+def _i32(xs):
+    return (ctypes.c_int * len(xs))(*[int(x) for x in xs])
+
+
+class Plan:
+    """Owning handle of an rtr_plan."""
+
+    def __init__(self, handle, dims, K, R, params):
+        self.handle = handle
+        self.dims = tuple(int(d) for d in dims)
+        self.N = len(self.dims)
+        self.R = tuple(int(r) for r in R)
+        self.params = params
+        ke = (ctypes.c_int * self.N)()
+        order = (ctypes.c_int * self.N)()
+        _check(lib().rtr_plan_info(handle, ke, order))
+        self.K = tuple(ke)
+        self.order = tuple(order)
+        self.prec = params.prec
+        self.x_dtype = torch.float64 if params.prec == RTR_FP64 else torch.float32
+        self.projected = tuple(k < d for k, d in zip(self.K, self.dims))
+
+    def close(self):
+        if self.handle:
+            lib().rtr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rtr_params_default():
+    p = Params()
+    lib().rtr_params_default(ctypes.byref(p))
+    return p
+
+
+def make_params(prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None):
+    p = rtr_params_default()
+    p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    p.seed = int(seed)
+    p.sweeps = int(sweeps)
+    p.tol = float(tol)
+    if chain_order is not None:
+        for i, m in enumerate(chain_order):
+            p.chain_order[i] = int(m)
+    return p
+
+
+def rtr_plan_create(dims, K, R, params):
+    h = _VP()
+    N = len(dims)
+    _check(lib().rtr_plan_create(ctypes.byref(h), N, _i64(dims), _i32(K), _i32(R), ctypes.byref(params)))
+    return Plan(h, dims, K, R, params)
+
+
+def rtr_plan_destroy(plan):
+    plan.close()
+
+
+def rtr_plan_flags(plan):
+    f = ctypes.c_int(0)
+    _check(lib().rtr_plan_flags(plan.handle, ctypes.byref(f)))
+    return f.value
+
+
+def rtr_sketch(plan, X, Y, stream=None):
+    _dev(X, plan.x_dtype, "X")
+    _check(lib().rtr_sketch(plan.handle, _ptr(X), _ptrs(Y, torch.float64, "Y"), _stream(stream)))
+
+
+def rtr_project(plan, X, Y, Q, P, stream=None):
+    _dev(X, plan.x_dtype, "X")
+    _dev(P, plan.x_dtype, "P")
+    _check(lib().rtr_project(plan.handle, _ptr(X), _ptrs(Y, torch.float64, "Y"), _ptrs(Q, torch.float64, "Q"),
+                             _ptr(P), _stream(stream)))
+
+
+def rtr_als(plan, P, Z, init_given, err=None, stream=None):
+    _dev(P, plan.x_dtype, "P")
+    _dev(err, torch.float64, "err")
+    _check(lib().rtr_als(plan.handle, _ptr(P), _ptrs(Z, torch.float64, "Z"), int(bool(init_given)), _ptr(err),
+                         _stream(stream)))
+
+
+def rtr_svd(plan, P, tol, Z, ranks=None, stream=None):
+    _dev(P, plan.x_dtype, "P")
+    r = _i32(ranks if ranks is not None else [0] * plan.N)
+    _check(lib().rtr_svd(plan.handle, _ptr(P), float(tol), _ptrs(Z, torch.float64, "Z"), r, _stream(stream)))
+    return list(r)
+
+
+def rtr_backproject(plan, Z, Q, G, ranks=None, stream=None):
+    r = None if ranks is None else _i32(ranks)
+    _check(lib().rtr_backproject(plan.handle, _ptrs(Z, torch.float64, "Z"), _ptrs(Q, torch.float64, "Q"),
+                                 _ptrs(G, torch.float64, "G"), r, _stream(stream)))
+
+
+def rtr_reconstruct_work_bytes(dims, R):
+    return int(lib().rtr_reconstruct_work_bytes(len(dims), _i64(dims), _i32(R)))
+
+
+def rtr_reconstruct(dims, R, G, out_prec, Xhat, work, stream=None):
+    op = PREC[out_prec] if isinstance(out_prec, str) else int(out_prec)
+    _dev(Xhat, torch.float64 if op == RTR_FP64 else torch.float32, "Xhat")
+    _dev(work, None, "work")
+    _check(lib().rtr_reconstruct(len(dims), _i64(dims), _i32(R), _ptrs(G, torch.float64, "G"), op, _ptr(Xhat),
+                                 _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def rtr_rse(plan, P, Z, out, ranks=None, stream=None):
+    _dev(P, plan.x_dtype, "P")
+    _dev(out, torch.float64, "out")
+    r = None if ranks is None else _i32(ranks)
+    _check(lib().rtr_rse(plan.handle, _ptr(P), _ptrs(Z, torch.float64, "Z"), r, _ptr(out), _stream(stream)))
+
+
+def rtr_draw_omega(plan, mode, row0, nrows, K, out, stream=None):
+    _dev(out, torch.float64, "out")
+    _check(lib().rtr_draw_omega(plan.handle, int(mode), int(row0), int(nrows), int(K), _ptr(out), _stream(stream)))
+
+
+def rtr_gaussian_table(prec):
+    out = (ctypes.c_double * 4096)()
+    op = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(lib().rtr_gaussian_table(op, out))
+    return np.frombuffer(out, dtype=np.float64).copy()
