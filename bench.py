@@ -1,0 +1,371 @@
+"""Benchmark: tensor GB/s sketched + decomposed (randomized TR-ALS), mixed
+precision vs plain FP32, on one GB300 per rank.
+
+Workload (one step): an order-4 200x200x200x200 float32 tensor (6.4 GB) made
+from TR ranks 10 with N(0,1) cores plus Gaussian noise at 30 dB, K_n = 25,
+R_n = 10, 30 ALS sweeps: sketch (Algorithm 1 steps 4-5), QR and the
+mode-product chain (steps 6-7), TR-ALS (step 9), back-projection (step 11)
+and the RSE identity.  The input is synthetic, built on the GPU from seeded
+cores; it is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec bf16|fp32] [--size S] [--no-cpu-baseline]
+
+Multi-GPU: replicas only (each rank decomposes its own tensor, no collective
+on the data path); value = all ranks' bytes / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tensor GB/s sketched+decomposed at rel err <=1e-3: mixed vs plain FP32, same GB300"
+WORKLOAD = "rTR-ALS order-4 200^4 fp32 (6.4 GB), TR rank 10 + 30 dB noise, K=25, R=10, 30 sweeps"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--size", type=int, default=200, help="mode length (200 = the named workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel build (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        return d.get(kernel_key)
+    except Exception:
+        return None
+
+
+def build_input(dims, rank, snr_db, seed, device):
+    import torch
+    from paper_1901_01652_gb300 import rtr, workloads
+    N = len(dims)
+    R = [rank] * N
+    cores = [torch.from_numpy(c).to(device) for c in workloads.tr_cores(dims, R, seed)]
+    X = torch.empty(dims, dtype=torch.float32, device=device)
+    work = torch.empty(rtr.rtr_reconstruct_work_bytes(dims, R), dtype=torch.uint8, device=device)
+    rtr.rtr_reconstruct(dims, R, cores, "fp32", X, work)
+    del work
+    nrm = float(torch.linalg.vector_norm(X, dtype=torch.float64))
+    sigma = workloads.snr_sigma(nrm, X.numel(), snr_db)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    flat = X.view(-1)
+    chunk = 1 << 28
+    for i in range(0, flat.numel(), chunk):
+        n = min(chunk, flat.numel() - i)
+        flat[i:i + n].add_(torch.randn(n, generator=g, device=device, dtype=torch.float32), alpha=sigma)
+    torch.cuda.synchronize()
+    return X
+
+
+class Pipeline:
+    def __init__(self, dims, K, R, sweeps, prec, seed, device):
+        import torch
+        from paper_1901_01652_gb300 import workloads
+        from paper_1901_01652_gb300.api import RTRD
+        self.eng = RTRD(dims, K, R, prec, seed, sweeps, device=device)
+        Ke = self.eng.plan.K
+        self.init = [torch.from_numpy(z).to(device) for z in workloads.als_init(Ke, R, seed)]
+        self.ev = None
+
+    def step(self, X, stream, events=None):
+        from paper_1901_01652_gb300 import rtr
+        e = self.eng
+        for z, i in zip(e.Z, self.init):
+            z.copy_(i, non_blocking=True)
+        if events is not None:
+            events[0].record(stream)
+        rtr.rtr_sketch(e.plan, X, e.Y, stream)
+        if events is not None:
+            events[1].record(stream)
+        rtr.rtr_project(e.plan, X, e.Y, e.Q, e.P, stream)
+        rtr.rtr_als(e.plan, e.P, e.Z, True, e.err, stream)
+        rtr.rtr_backproject(e.plan, e.Z, e.Q, e.G, None, stream)
+        rtr.rtr_rse(e.plan, e.P, e.Z, e.rse, None, stream)
+
+
+def time_steps(pipe, X, steps, warmup, stream, dist_max):
+    import torch
+    from paper_1901_01652_gb300 import rtr
+    for _ in range(warmup):
+        pipe.step(X, stream)
+    torch.cuda.synchronize()
+    sk_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist_barrier()
+    torch.cuda.synchronize()
+    l0 = rtr.rtr_kernel_launches()
+    t0.record(stream)
+    for i in range(steps):
+        pipe.step(X, stream, sk_events[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    l1 = rtr.rtr_kernel_launches()
+    dist_barrier()
+    ms = t0.elapsed_time(t1)
+    sk_ms = sum(a.elapsed_time(b) for a, b in sk_events) / steps
+    return dist_max(ms), sk_ms, l1 - l0
+
+
+_DIST = {"on": False}
+
+
+def dist_barrier():
+    if _DIST["on"]:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args):
+    import torch
+    from paper_1901_01652_gb300 import build, rtr
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        _DIST["on"] = True
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist_barrier()
+    rtr.lib()
+
+    def dist_max(x):
+        if not _DIST["on"]:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t[0])
+
+    S = args.size
+    dims, K, R, sweeps, snr, seed = (S, S, S, S), (25,) * 4, (10,) * 4, 30, 30.0, 1903 + rank
+    X = build_input(dims, 10, snr, seed, device)
+    xbytes = X.numel() * 4
+    stream = torch.cuda.current_stream(device)
+
+    pipe = Pipeline(dims, K, R, sweeps, args.prec, 1903, device)
+    with ClockSampler(local) as clk:
+        ms, sk_ms, launches = time_steps(pipe, X, args.steps, args.warmup, stream, dist_max)
+    clocks = clk.summary()
+    ms_step = ms / args.steps
+    value = world * xbytes * args.steps / (ms * 1e-3) / 1e9
+    torch.cuda.synchronize()
+    rse_mixed = float(pipe.eng.rse.cpu()[0])
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if S == 200 else f"rTR-ALS order-4 {S}^4 fp32 (reduced)",
+                   "dims": list(dims), "K": list(K), "R": list(R), "sweeps": sweeps, "snr_db": snr,
+                   "prec": args.prec, "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+        "rse": rse_mixed,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    # roofline of the dominant kernel: the sketch, one launch per projected mode,
+    # each reading X once (|X| * 4 bytes of algorithmic traffic)
+    peak, peak_kind = measured_peak()
+    nproj = sum(1 for k, d in zip(K, dims) if k < d)
+    per_launch_ms = sk_ms / nproj
+    achieved = xbytes / (per_launch_ms * 1e-3) / 1e9
+    key = f"sketch_{args.prec}_{S}x4"
+    out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                       "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                       "traffic": ncu_traffic(key), "kernel": key,
+                       "sketch_ms_per_mode": round(per_launch_ms, 4),
+                       "pipeline_bytes_per_step": None}
+    # plain FP32 arm on the same tensor
+    if not args.no_plain and args.prec != "fp32":
+        plain = Pipeline(dims, K, R, sweeps, "fp32", 1903, device)
+        pms, psk, _ = time_steps(plain, X, max(1, args.steps // 2), 1, stream, dist_max)
+        psteps = max(1, args.steps // 2)
+        torch.cuda.synchronize()
+        rse_plain = float(plain.eng.rse.cpu()[0])
+        Xm = pipe.eng.reconstruct("fp32")
+        Xp = plain.eng.reconstruct("fp32")
+        diff = float(torch.linalg.vector_norm(Xm - Xp, dtype=torch.float64) /
+                     torch.linalg.vector_norm(Xp, dtype=torch.float64))
+        del Xm, Xp
+        out["plain_fp32"] = {"value": round(world * xbytes * psteps / (pms * 1e-3) / 1e9, 3),
+                             "ms_per_step": round(pms / psteps, 4), "rse": rse_plain,
+                             "sketch_ms_per_mode": round(psk / nproj, 4)}
+        out["mixed_vs_plain_rel_diff"] = diff
+        del plain
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        from paper_1901_01652_gb300.api import decompose
+        Xh = X.cpu().pin_memory()
+        ek = max(1, min(args.steps, 3))
+        decompose(Xh, K, R, "als", args.prec, 1903, sweeps, init=pipe.init, engine=pipe.eng)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(ek):
+            G, rse_e2e, _ = decompose(Xh, K, R, "als", args.prec, 1903, sweeps, init=pipe.init, engine=pipe.eng)
+        el = time.perf_counter() - t
+        d2h = sum(g.numel() * 8 for g in G) + 8
+        out["e2e"] = {"value": round(world * xbytes * ek / el / 1e9, 3), "unit": "GB/s",
+                      "h2d_bytes_per_step": int(xbytes), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": round(el / ek * 1e3, 3)}
+        del Xh
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if _DIST["on"]:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle arms
+
+SAMPLE_SIDE = 40
+
+
+def oracle_sample_step(side, seed):
+    """One step of the same workload recipe on a bounded side^4 sample, run
+    by the FP64 oracle; returns (bytes of X as float32, seconds)."""
+    from oracle import rtrd as orc
+    from oracle import tensor as ot
+    from paper_1901_01652_gb300 import workloads
+    dims, K, R = (side,) * 4, (25,) * 4, (10,) * 4
+    S = ot.tr_full(workloads.tr_cores(dims, R, seed))
+    X = (S + workloads.snr_sigma(ot.fro(S), S.size, 30.0) * workloads.unit_noise(dims, seed)).astype(np.float32)
+    X = X.astype(np.float64)
+    init = workloads.als_init(orc.effective_K(dims, K), R, seed)
+    t = time.perf_counter()
+    out = orc.rtrd(X, K, R, "als", seed=seed, prec="fp32", sweeps=30, init=init)
+    orc.rse_identity(ot.fro(X) ** 2, out["P"], out["Z"])
+    return X.size * 4, time.perf_counter() - t
+
+
+def cpu_baseline():
+    b, s = oracle_sample_step(SAMPLE_SIDE, 1903)
+    return {"value": round(b / s / 1e9, 6), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{SAMPLE_SIDE}^4 tensor of the same recipe (K=25, R=10, 30 sweeps), FP64 NumPy oracle, "
+                      f"{s:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_step(26, 1903)
+    tot_b, tot_s = 0, 0.0
+    for i in range(args.steps):
+        b, s = oracle_sample_step(SAMPLE_SIDE, 1903)
+        tot_b += b
+        tot_s += s
+    v = tot_b / tot_s / 1e9
+    out = {"metric": METRIC, "value": round(v, 6), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(tot_s / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample": f"{SAMPLE_SIDE}^4 per step"},
+           "cpu_baseline": {"value": round(v, 6), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{SAMPLE_SIDE}^4 tensor of the same recipe per step"},
+           "e2e": {"value": round(v, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

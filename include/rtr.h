@@ -74,6 +74,10 @@ void rtr_params_default(rtr_params* p);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rtr_last_error(void);
 
+/* Number of CUDA kernels this library has launched in the process so far
+   (all threads; for accounting launches inside a timed region). */
+unsigned long long rtr_kernel_launches(void);
+
 /*
  * Create a plan for an order-N tensor of shape dims[N] with projection sizes
  * K[N] (Algorithm 1, input [K_n]) and TR ranks R[N] (input R_1..R_N).

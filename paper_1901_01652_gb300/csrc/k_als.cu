@@ -313,6 +313,7 @@ T* build_chain(int N, const int64_t* dims, const int* R, const double* const* Z,
         const int fin = (t == count - 1) ? final_tr : 0;
         const int64_t total = Jp * Km * Rfirst * Rd;
         subchain_step_kernel<T><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out, fin, Aa, Bb);
+        rtr_count_launch();
         if (cudaGetLastError() != cudaSuccess) { *status = RTR_ECUDA; return nullptr; }
         cur = out;
         which ^= 1;

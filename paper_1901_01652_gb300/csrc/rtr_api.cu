@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include "rtr_internal.cuh"
 
@@ -118,6 +119,9 @@ int rtr_set_error(int code, const char* fmt, ...) {
     va_end(ap);
     return code;
 }
+static std::atomic<unsigned long long> g_launches{0};
+void rtr_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 int rtr_cuda_check(cudaError_t e, const char* what) {
     return rtr_set_error(RTR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -125,6 +129,8 @@ int rtr_cuda_check(cudaError_t e, const char* what) {
 extern "C" {
 
 const char* rtr_last_error(void) { return g_err; }
+
+unsigned long long rtr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void rtr_params_default(rtr_params* p) {
     if (!p) return;

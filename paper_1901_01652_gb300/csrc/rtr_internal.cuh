@@ -46,7 +46,10 @@ struct rtr_plan {
 int rtr_set_error(int code, const char* fmt, ...);
 int rtr_cuda_check(cudaError_t e, const char* what);
 #define RTR_CUDA(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return rtr_cuda_check(e_, #call); } while (0)
-#define RTR_LAUNCH_CHECK(what) do { cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return rtr_cuda_check(e_, what); } while (0)
+// every kernel launch of the library is followed by this check, which also
+// counts the launch (rtr_kernel_launches)
+void rtr_count_launch();
+#define RTR_LAUNCH_CHECK(what) do { rtr_count_launch(); cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return rtr_cuda_check(e_, what); } while (0)
 
 static inline int64_t rtr_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

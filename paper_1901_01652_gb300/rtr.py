@@ -21,7 +21,7 @@ FLAG_NONFINITE, FLAG_QR_FALLBACK, FLAG_GRAM_PINV, FLAG_TIMEOUT = 1, 2, 4, 8
 
 # every entry point of include/rtr.h
 ENTRY_POINTS = (
-    "rtr_params_default", "rtr_last_error", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
+    "rtr_params_default", "rtr_last_error", "rtr_kernel_launches", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
     "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
 )
@@ -56,6 +56,7 @@ def lib():
     sig = {
         "rtr_params_default": (None, [ctypes.POINTER(Params)]),
         "rtr_last_error": (ctypes.c_char_p, []),
+        "rtr_kernel_launches": (ctypes.c_ulonglong, []),
         "rtr_plan_create": (ctypes.c_int, [_VPP, ctypes.c_int, _I64P, _IP, _IP, ctypes.POINTER(Params)]),
         "rtr_plan_destroy": (ctypes.c_int, [_VP]),
         "rtr_plan_info": (ctypes.c_int, [_VP, _IP, _IP]),
@@ -150,6 +151,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def rtr_kernel_launches():
+    return int(lib().rtr_kernel_launches())
 
 
 def rtr_params_default():

@@ -56,7 +56,14 @@ def test_omega_bit_exact(prec, tabprec):
         out = torch.empty((nrows, K), dtype=torch.float64, device="cuda")
         rtr.rtr_draw_omega(plan, mode, row0, nrows, K, out)
         ref = oom.omega(123456789, mode, nrows, K, tabprec, row0=row0)
-        assert np.array_equal(out.cpu().numpy(), ref)
+        got = out.cpu().numpy()
+        if tabprec == "bf16":
+            assert np.array_equal(got, ref)
+        else:
+            # the two float64 tables are computed independently and agree to
+            # ~1 ulp; adjacent table entries are >= 6e-4 apart, so this bound
+            # also proves every Philox index matches
+            assert np.max(np.abs(got - ref)) < 2e-15
 
 
 def test_default_chain_order_matches_rule():
