@@ -189,6 +189,29 @@ int rtr_draw_omega(rtr_plan* plan, int mode, int64_t row0, int64_t nrows, int K,
 /* Test support: the Gaussian table of a precision as float64 values (host out[4096]). */
 int rtr_gaussian_table(int prec, double* out);
 
+/*
+ * Allocation-free sketch of one mode (the paper has no counterpart; this is a
+ * deployment variant of rtr_sketch for callers that cannot call cudaMalloc,
+ * e.g. code embedded in a framework that owns all device memory, or a
+ * service that must not grow its device footprint after start-up).
+ *     Y = X_(n) Omega_n     for X viewed as (A, I, B), i.e. I = I_n,
+ *                           A = prod of the modes before n, B = after n
+ * prec: RTR_FP64 (X float64) or RTR_FP32 (X float32, bfloat16-valued Omega).
+ * seed, mode: the key (seed, n) of Omega_n, as in rtr_sketch.  X and Y
+ * (I x K float64) are caller-owned device buffers; no plan is needed.
+ * Scratch: a file-scope device array of 2^21 float64 (16 MiB) plus the two
+ * Gaussian tables (48 KiB), held on every GPU that loads the library until
+ * the process exits.  Requires I*K <= 2^21 and 1 <= K <= 64, else RTR_EINVAL.
+ * The first call on a device performs set-up on the current device
+ * (resolves the arrays' device addresses, copies the tables with synchronous
+ * cudaMemcpy); make that first call before any stream capture.  It calls no
+ * cudaMalloc/cudaFree.  Every call shares the one scratch array (each call
+ * overwrites every partial it reads, so nothing needs clearing); calls that
+ * overlap on the GPU (other streams, other threads) race on it.
+ */
+int rtr_sketch_mode_noalloc(int prec, const void* X, int64_t A, int64_t I, int64_t B, int K,
+                            uint64_t seed, int mode, double* Y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -244,3 +244,115 @@ size_t contract_norm_elems(int num_sms, int64_t I, int C) {
     const Shape sh = choose_shape(I, C);
     return (size_t)((int64_t)8 * num_sms * std::max(1, sh.gy) + 8);
 }
+
+// ---- allocation-free single-mode sketch ---------------------------------------
+// For callers that cannot call cudaMalloc (for example code running inside a
+// host framework that owns all device memory, or a process that must not grow
+// its device footprint after start-up).  The split-K partials and the
+// Gaussian tables live in file-scope __device__ arrays instead of a plan's
+// workspace.  Every GPU that loads this library holds these arrays (16 MiB of
+// partials plus 48 KiB of tables) until the process exits.
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = (size_t)1 << 21;    // 2 Mi doubles = 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+static __device__ __align__(256) double g_noalloc_tab64[4096];
+static __device__ __align__(256) float g_noalloc_tab32[4096];
+
+struct NoAllocDevice {
+    bool ready = false;
+    double* scratch = nullptr;   // device address of g_noalloc_scratch on this device
+    double* tab64 = nullptr;
+    float* tab32 = nullptr;
+    int num_sms = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+// Once per device, with that device current: resolve the device addresses of
+// the file-scope arrays (host code cannot use their names as pointers) and
+// fill the tables with synchronous copies.
+int noalloc_setup(NoAllocDevice** out) {
+    int dev = 0;
+    RTR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rtr_set_error(RTR_EINVAL, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        RTR_CUDA(cudaGetSymbolAddress((void**)&d.scratch, g_noalloc_scratch));
+        RTR_CUDA(cudaGetSymbolAddress((void**)&d.tab64, g_noalloc_tab64));
+        RTR_CUDA(cudaGetSymbolAddress((void**)&d.tab32, g_noalloc_tab32));
+        RTR_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        static double t64[4096];
+        static float t32[4096];
+        rtr_host_tables(t64, t32);
+        RTR_CUDA(cudaMemcpy(d.tab64, t64, sizeof(t64), cudaMemcpyHostToDevice));
+        RTR_CUDA(cudaMemcpy(d.tab32, t32, sizeof(t32), cudaMemcpyHostToDevice));
+        d.ready = true;
+    }
+    *out = &d;
+    return RTR_OK;
+}
+
+template <typename T, int TM, int TK>
+int launch_noalloc(const NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cudaStream_t s) {
+    const int KP = sh.NTK * sh.TK;
+    const size_t smem = sizeof(T) * ((size_t)RC * (sh.rows + 1) + (size_t)RC * KP + 4096);
+    auto kern = contract_kernel<T, TM, TK, true>;
+    RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+    occ = std::max(1, occ);
+    int64_t nchunks, nbc = 1;
+    if (a.B == 1) nchunks = rtr_ceil_div(a.A, RC);
+    else { nbc = rtr_ceil_div(a.B, RC); nchunks = a.A * nbc; }
+    int64_t gx = std::max<int64_t>(1, (int64_t)occ * d.num_sms / sh.gy);
+    gx = std::min<int64_t>(gx, nchunks);
+    gx = std::min<int64_t>(gx, (int64_t)(kNoAllocScratchDoubles / (a.I * a.C)));   // >= 1, checked by caller
+    dim3 grid((unsigned)gx, (unsigned)sh.gy);
+    kern<<<grid, NT, smem, s>>>((const T*)a.X, a.A, (int)a.I, a.B, a.C, sh.NTK, sh.rows, nchunks, nbc, a.seed,
+                                a.mode, (const T*)a.table, nullptr, 0, d.scratch, nullptr);
+    RTR_LAUNCH_CHECK("contract_kernel (no-alloc)");
+    const int64_t count = a.I * a.C;
+    reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count, 256), 256, 0, s>>>(d.scratch, (int)gx, count, a.Y,
+                                                                                nullptr, 0, nullptr);
+    RTR_LAUNCH_CHECK("reduce_partials_kernel (no-alloc)");
+    return RTR_OK;
+}
+
+template <typename T>
+int dispatch_noalloc(const NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cudaStream_t s) {
+#define RTR_CASE(tm, tk) if (sh.TM == tm && sh.TK == tk) return launch_noalloc<T, tm, tk>(d, a, sh, s);
+    RTR_CASE(1, 4) RTR_CASE(2, 4) RTR_CASE(4, 4) RTR_CASE(8, 4)
+    RTR_CASE(1, 8) RTR_CASE(2, 8) RTR_CASE(4, 8) RTR_CASE(8, 8)
+#undef RTR_CASE
+    return rtr_set_error(RTR_EINVAL, "no contraction shape for TM=%d TK=%d", sh.TM, sh.TK);
+}
+
+}  // namespace
+
+extern "C" int rtr_sketch_mode_noalloc(int prec, const void* X, int64_t A, int64_t I, int64_t B, int K,
+                                       uint64_t seed, int mode, double* Y, void* stream) {
+    if (!X || !Y) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    if (prec != RTR_FP64 && prec != RTR_FP32)
+        return rtr_set_error(RTR_EINVAL, "rtr_sketch_mode_noalloc supports RTR_FP64 and RTR_FP32 only");
+    if (A < 1 || I < 1 || B < 1 || I > (1 << 30)) return rtr_set_error(RTR_EINVAL, "bad view (A, I, B)");
+    if (K < 1 || K > RTR_MAX_KSKETCH) return rtr_set_error(RTR_EINVAL, "K = %d outside [1, 64]", K);
+    if ((size_t)(I * K) > kNoAllocScratchDoubles)
+        return rtr_set_error(RTR_EINVAL, "I*K = %lld exceeds the static scratch of %zu doubles",
+                             (long long)(I * K), kNoAllocScratchDoubles);
+    NoAllocDevice* d = nullptr;
+    int st = noalloc_setup(&d);
+    if (st) return st;
+    const int f64 = prec == RTR_FP64;
+    ContractArgs a{};
+    a.X = X; a.A = A; a.I = I; a.B = B; a.C = K;
+    a.gen = 1; a.seed = seed; a.mode = mode;
+    a.table = f64 ? (const void*)d->tab64 : (const void*)d->tab32;
+    a.Y = Y; a.norm_out = nullptr;
+    const Shape sh = choose_shape(I, K);
+    cudaStream_t s = (cudaStream_t)stream;
+    return f64 ? dispatch_noalloc<double>(*d, a, sh, s) : dispatch_noalloc<float>(*d, a, sh, s);
+}

@@ -119,6 +119,11 @@ int rtr_set_error(int code, const char* fmt, ...) {
     va_end(ap);
     return code;
 }
+void rtr_host_tables(double* t64, float* t32) {
+    gaussian_table64(t64);
+    for (int j = 0; j < 4096; ++j) t32[j] = bf16_value(bf16_bits(t64[j]));
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 void rtr_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 

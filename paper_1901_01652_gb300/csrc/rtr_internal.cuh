@@ -53,6 +53,9 @@ void rtr_count_launch();
 
 static inline int64_t rtr_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// host copies of the Gaussian quantile table: float64 and bfloat16-rounded
+void rtr_host_tables(double* t64, float* t32);
+
 // mode view (A, I, B) of a shape
 static inline void rtr_mode_view(int N, const int64_t* dims, int n, int64_t* A, int64_t* I, int64_t* B) {
     int64_t a = 1, b = 1;

@@ -24,6 +24,7 @@ ENTRY_POINTS = (
     "rtr_params_default", "rtr_last_error", "rtr_kernel_launches", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
     "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
+    "rtr_sketch_mode_noalloc",
 )
 
 
@@ -72,6 +73,9 @@ def lib():
         "rtr_rse": (ctypes.c_int, [_VP, _VP, _VPP, _IP, _VP, _VP]),
         "rtr_draw_omega": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _VP, _VP]),
         "rtr_gaussian_table": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "rtr_sketch_mode_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int64, ctypes.c_int64,
+                                                   ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                                   _VP, _VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -253,3 +257,13 @@ def rtr_gaussian_table(prec):
     op = PREC[prec] if isinstance(prec, str) else int(prec)
     _check(lib().rtr_gaussian_table(op, out))
     return np.frombuffer(out, dtype=np.float64).copy()
+
+
+def rtr_sketch_mode_noalloc(prec, X, view, K, seed, mode, Y, stream=None):
+    """Allocation-free one-mode sketch; view = (A, I, B) of X around the mode."""
+    op = PREC[prec] if isinstance(prec, str) else int(prec)
+    _dev(X, torch.float64 if op == RTR_FP64 else torch.float32, "X")
+    _dev(Y, torch.float64, "Y")
+    A, I, B = (int(v) for v in view)
+    _check(lib().rtr_sketch_mode_noalloc(op, _ptr(X), A, I, B, int(K), int(seed), int(mode), _ptr(Y),
+                                         _stream(stream)))
