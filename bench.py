@@ -161,15 +161,17 @@ class Pipeline:
         e = self.eng
         for z, i in zip(e.Z, self.init):
             z.copy_(i, non_blocking=True)
-        if events is not None:
-            events[0].record(stream)
+        rec = (lambda i: events[i].record(stream)) if events is not None else (lambda i: None)
+        rec(0)
         rtr.rtr_sketch(e.plan, X, e.Y, stream)
-        if events is not None:
-            events[1].record(stream)
+        rec(1)
         rtr.rtr_project(e.plan, X, e.Y, e.Q, e.P, stream)
+        rec(2)
         rtr.rtr_als(e.plan, e.P, e.Z, True, e.err, stream)
+        rec(3)
         rtr.rtr_backproject(e.plan, e.Z, e.Q, e.G, None, stream)
         rtr.rtr_rse(e.plan, e.P, e.Z, e.rse, None, stream)
+        rec(4)
 
 
 def time_steps(pipe, X, steps, warmup, stream, dist_max):
@@ -178,7 +180,7 @@ def time_steps(pipe, X, steps, warmup, stream, dist_max):
     for _ in range(warmup):
         pipe.step(X, stream)
     torch.cuda.synchronize()
-    sk_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sk_events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dist_barrier()
     torch.cuda.synchronize()
@@ -191,8 +193,8 @@ def time_steps(pipe, X, steps, warmup, stream, dist_max):
     l1 = rtr.rtr_kernel_launches()
     dist_barrier()
     ms = t0.elapsed_time(t1)
-    sk_ms = sum(a.elapsed_time(b) for a, b in sk_events) / steps
-    return dist_max(ms), sk_ms, l1 - l0
+    phases = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in sk_events) / steps for i in range(4)]
+    return dist_max(ms), phases, l1 - l0
 
 
 _DIST = {"on": False}
@@ -239,7 +241,8 @@ def run_ours(args):
 
     pipe = Pipeline(dims, K, R, sweeps, args.prec, 1903, device)
     with ClockSampler(local) as clk:
-        ms, sk_ms, launches = time_steps(pipe, X, args.steps, args.warmup, stream, dist_max)
+        ms, phases, launches = time_steps(pipe, X, args.steps, args.warmup, stream, dist_max)
+    sk_ms = phases[0]
     clocks = clk.summary()
     ms_step = ms / args.steps
     value = world * xbytes * args.steps / (ms * 1e-3) / 1e9
@@ -255,6 +258,8 @@ def run_ours(args):
                    "dims": list(dims), "K": list(K), "R": list(R), "sweeps": sweeps, "snr_db": snr,
                    "prec": args.prec, "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
         "rse": rse_mixed,
+        "phases_ms": {"sketch": round(phases[0], 4), "project": round(phases[1], 4), "als": round(phases[2], 4),
+                      "backproject_rse": round(phases[3], 4)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
@@ -273,7 +278,8 @@ def run_ours(args):
     # plain FP32 arm on the same tensor
     if not args.no_plain and args.prec != "fp32":
         plain = Pipeline(dims, K, R, sweeps, "fp32", 1903, device)
-        pms, psk, _ = time_steps(plain, X, max(1, args.steps // 2), 1, stream, dist_max)
+        pms, pph, _ = time_steps(plain, X, max(1, args.steps // 2), 1, stream, dist_max)
+        psk = pph[0]
         psteps = max(1, args.steps // 2)
         torch.cuda.synchronize()
         rse_plain = float(plain.eng.rse.cpu()[0])
@@ -284,7 +290,9 @@ def run_ours(args):
         del Xm, Xp
         out["plain_fp32"] = {"value": round(world * xbytes * psteps / (pms * 1e-3) / 1e9, 3),
                              "ms_per_step": round(pms / psteps, 4), "rse": rse_plain,
-                             "sketch_ms_per_mode": round(psk / nproj, 4)}
+                             "sketch_ms_per_mode": round(psk / nproj, 4),
+                             "phases_ms": {"sketch": round(pph[0], 4), "project": round(pph[1], 4),
+                                           "als": round(pph[2], 4), "backproject_rse": round(pph[3], 4)}}
         out["mixed_vs_plain_rel_diff"] = diff
         del plain
     # end to end through the public API with host buffers

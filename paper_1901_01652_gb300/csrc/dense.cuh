@@ -5,33 +5,41 @@
 namespace rtr {
 
 // In-place lower Cholesky G = L L^T of an n x n SPD matrix (row-major, ld,
-// n <= 256).  Returns false (uniformly across the block) if a pivot is not
-// finite or not above rel_tol times the original diagonal entry (rel_tol = 0
-// is the LAPACK potrf failure condition, pivot <= 0).
-__device__ inline bool block_cholesky(double* G, int n, int ld, double rel_tol = 0.0) {
-    __shared__ int fail;
-    __shared__ double diag0[256];
-    if (threadIdx.x == 0) fail = 0;
+// n <= 256, blockDim.x a multiple of 16).  Returns false (uniformly across the
+// block) if a pivot is not finite or not above rel_tol times the original
+// diagonal entry (rel_tol = 0 is the LAPACK potrf failure condition, pivot <= 0).
+// Right-looking, one barrier per column: step k updates the trailing matrix
+// from the unscaled column k (scaled by 1/d_k), and scales column k-1 and
+// writes its diagonal, which no thread reads during step k.
+template <typename T>
+__device__ inline bool block_cholesky(T* G, int n, int ld, double rel_tol = 0.0) {
+    __shared__ T diag0[256];
     for (int k = threadIdx.x; k < n; k += blockDim.x) diag0[k] = G[k * ld + k];
     __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4, nty = blockDim.x >> 4;
+    T inv_prev = T(0), sq_prev = T(0);
     for (int k = 0; k < n; ++k) {
-        if (threadIdx.x == 0) {
-            const double d = G[k * ld + k];
-            if (!(d > rel_tol * diag0[k]) || !(d > 0.0) || !isfinite(d)) fail = 1;
-            else G[k * ld + k] = sqrt(d);
+        const T d = G[k * ld + k];
+        // compared in T: a float64 conversion here would run on the slow
+        // float64 pipe in every thread at every column
+        if (!(d > (T)rel_tol * diag0[k]) || !(d > T(0)) || !isfinite(d)) return false;
+        const T sq = sqrt(d);
+        const T inv = T(1) / sq;
+        const T inv2 = inv * inv;
+        if (k > 0) {
+            for (int i = k + threadIdx.x; i < n; i += blockDim.x) G[i * ld + k - 1] *= inv_prev;
+            if (threadIdx.x == 0) G[(k - 1) * ld + k - 1] = sq_prev;
         }
-        __syncthreads();
-        if (fail) return false;
-        const double piv = G[k * ld + k];
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) G[i * ld + k] /= piv;
-        __syncthreads();
-        const int m = n - k - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-            if (j <= i) G[i * ld + j] -= G[i * ld + k] * G[j * ld + k];
+        for (int i = k + 1 + ty; i < n; i += nty) {
+            const T gik = G[i * ld + k] * inv2;
+            for (int j = k + 1 + tx; j <= i; j += 16) G[i * ld + j] -= gik * G[j * ld + k];
         }
+        inv_prev = inv;
+        sq_prev = sq;
         __syncthreads();
     }
+    if (threadIdx.x == 0 && n > 0) G[(n - 1) * ld + n - 1] = sq_prev;
+    __syncthreads();
     return true;
 }
 

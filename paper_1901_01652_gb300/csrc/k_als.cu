@@ -12,6 +12,7 @@
 // product, the Cholesky factorisation and the solves are float64.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <type_traits>
 #include "rtr_internal.cuh"
 #include "dense.cuh"
@@ -24,10 +25,12 @@ namespace {
 // Sout[(j'*Km + i), beta, gamma] = sum_c Sprev[j', beta, c] * Z[c, i, gamma]
 // (Sprev == nullptr: Sout[i, beta, gamma] = Z[beta, i, gamma]).
 // With final_tr, row j = b*A + a of the cyclic order is stored at a*B + b.
+// With Zfirst set (and Sprev null), the previous level is the first core
+// itself, read in its own layout Zfirst[beta, j', c] (Jp = its mode length).
 template <typename T>
 __global__ void subchain_step_kernel(const T* __restrict__ Sprev, int64_t Jp, int Rb, int Rc,
                                      const double* __restrict__ Z, int Km, int Rd, T* __restrict__ Sout,
-                                     int final_tr, int64_t Aa, int64_t Bb) {
+                                     int final_tr, int64_t Aa, int64_t Bb, const double* __restrict__ Zfirst) {
     const int64_t total = Jp * Km * Rb * Rd;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -37,7 +40,12 @@ __global__ void subchain_step_kernel(const T* __restrict__ Sprev, int64_t Jp, in
         const int i = (int)(j % Km);
         const int64_t jp = j / Km;
         T v;
-        if (Sprev == nullptr) {
+        if (Zfirst != nullptr) {
+            T acc = T(0);
+            const double* zf = Zfirst + ((int64_t)be * Jp + jp) * Rc;
+            for (int c = 0; c < Rc; ++c) acc = fma((T)zf[c], (T)Z[((int64_t)c * Km + i) * Rd + g], acc);
+            v = acc;
+        } else if (Sprev == nullptr) {
             v = (T)Z[((int64_t)be * Km + i) * Rd + g];
         } else {
             T s = T(0);
@@ -63,15 +71,27 @@ __global__ void transfer_kernel(const double* __restrict__ Z, int Ra, int Km, in
     }
 }
 
-// C (m x n) = A (m x k) B (k x n), float64, one output per thread.
-__global__ void matmul_f64_kernel(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
-                                  int m, int k, int n) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += gridDim.x * blockDim.x) {
-        const int i = e / n, j = e % n;
-        double s = 0.0;
-        for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * n + j];
-        C[e] = s;
+// C (m x n) = A (m x k) B (k x n), float64.  8 x 8 output tiles per CTA (64
+// threads) so that the float64 work of one product spreads over every SM;
+// A rows and B columns of the tile are staged in shared memory (k <= 256).
+__global__ void __launch_bounds__(64) matmul_f64_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                        double* __restrict__ C, int m, int k, int n) {
+    __shared__ double As[8][257];
+    __shared__ double Bs[256][9];
+    const int i0 = blockIdx.y * 8, j0 = blockIdx.x * 8;
+    for (int e = threadIdx.x; e < 8 * k; e += 64) {
+        const int r = e / k, l = e % k;
+        As[r][l] = (i0 + r < m) ? A[(int64_t)(i0 + r) * k + l] : 0.0;
     }
+    for (int e = threadIdx.x; e < 8 * k; e += 64) {
+        const int l = e / 8, c = e % 8;
+        Bs[l][c] = (j0 + c < n) ? B[(int64_t)l * n + j0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int r = threadIdx.x / 8, c = threadIdx.x % 8;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s += As[r][l] * Bs[l][c];
+    if (i0 + r < m && j0 + c < n) C[(int64_t)(i0 + r) * n + j0 + c] = s;
 }
 
 __global__ void trace_kernel(const double* __restrict__ M, int n, double* __restrict__ out) {
@@ -82,14 +102,397 @@ __global__ void trace_kernel(const double* __restrict__ M, int n, double* __rest
     }
 }
 
-// Solve z_i G = w_i for all i (G from Mprod by the (beta,alpha) reindexing),
-// write Z_n[alpha, i, beta] = z_i[beta*Rn + alpha]; err2 = ||P||^2 - sum z.w.
-// G in dynamic shared memory; fallback: Jacobi pseudo-inverse in global memory.
-__global__ void __launch_bounds__(512) als_solve_kernel(const double* __restrict__ Mprod, int Rn, int Rn1, int In,
-                                                        double* __restrict__ W, double* __restrict__ Wz,
-                                                        double* __restrict__ Zn, const double* __restrict__ normP2,
-                                                        double* __restrict__ err_out, double* __restrict__ jac_ws,
-                                                        int* __restrict__ flags) {
+// ---- fused subchain + contraction -------------------------------------------
+// W[i_n, (beta, alpha)] = sum_j P_<n>[i_n, j] S_j[beta, alpha] with the
+// subchain S_j = Z_{c_1}(i_{c_1}) ... Z_{c_{N-1}}(i_{c_{N-1}}) (c_t = n + t mod N)
+// generated on the fly: a CTA takes prefix indices (i_{c_1} .. i_{c_{N-2}}),
+// forms their product M (R_{n+1} x R_{c_{N-1}}) in shared memory, then for
+// blocks of the last index forms S rows = M Z_last(i) and accumulates the
+// outer products with the matching P entries.  One float64 partial per CTA.
+struct AlsContractArgs {
+    const void* P;
+    const void* Z[RTR_MAXN];          // cores in the compute type T
+    int64_t K[RTR_MAXN];
+    int64_t stride[RTR_MAXN];
+    int R[RTR_MAXN];
+    int cyc[RTR_MAXN];
+    int N, n;
+    int64_t Jpre;
+    double* partial;
+};
+
+constexpr int ALS_LB = 16;          // last-mode indices per block
+constexpr int ALS_MAXACC = 40;      // outputs per thread: K_n * C <= 256 * 40
+
+template <typename T>
+__global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, N = a.N;
+    const int Rb = a.R[(n + 1) % N], Rn = a.R[n];
+    const int C = Rb * Rn;
+    const int Kn = (int)a.K[n];
+    const int ml = a.cyc[N - 1];
+    const int Kl = (int)a.K[ml];
+    const int Rl = a.R[ml];                         // left rank of the last core
+    T* M0 = reinterpret_cast<T*>(smem_raw);          // Rb x 16
+    T* M1 = M0 + Rb * RTR_MAX_RANK;                  // Rb x 16
+    T* S = M1 + Rb * RTR_MAX_RANK;                   // ALS_LB x C
+    T* Pv = S + ALS_LB * C;                          // ALS_LB x Kn
+    const T* P = reinterpret_cast<const T*>(a.P);
+    const int tid = threadIdx.x;
+    const int nout = Kn * C;
+    T acc[ALS_MAXACC];
+#pragma unroll
+    for (int q = 0; q < ALS_MAXACC; ++q) acc[q] = T(0);
+
+    for (int64_t jp = blockIdx.x; jp < a.Jpre; jp += gridDim.x) {
+        // decode the prefix (row-major over c_1 .. c_{N-2}) and its P offset
+        int64_t rem = jp, base = 0;
+        int idx[RTR_MAXN];
+        for (int t = N - 2; t >= 1; --t) {
+            const int m = a.cyc[t];
+            idx[t] = (int)(rem % a.K[m]);
+            rem /= a.K[m];
+            base += idx[t] * a.stride[m];
+        }
+        // M = Z_{c_1}(i_1) ... Z_{c_{N-2}}(i_{N-2})
+        __syncthreads();
+        {
+            const int m = a.cyc[1];
+            const int Rc = a.R[(m + 1) % N];
+            for (int e = tid; e < Rb * Rc; e += blockDim.x) {
+                const int be = e / Rc, g = e % Rc;
+                M0[be * RTR_MAX_RANK + g] = reinterpret_cast<const T*>(a.Z[m])[((int64_t)be * a.K[m] + idx[1]) * Rc + g];
+            }
+        }
+        T* cur = M0;
+        T* nxt = M1;
+        for (int t = 2; t <= N - 2; ++t) {
+            __syncthreads();
+            const int m = a.cyc[t];
+            const int Rm = a.R[m], Rc = a.R[(m + 1) % N];
+            for (int e = tid; e < Rb * Rc; e += blockDim.x) {
+                const int be = e / Rc, g = e % Rc;
+                T sum = T(0);
+                for (int c = 0; c < Rm; ++c)
+                    sum = fma(cur[be * RTR_MAX_RANK + c], reinterpret_cast<const T*>(a.Z[m])[((int64_t)c * a.K[m] + idx[t]) * Rc + g], sum);
+                nxt[be * RTR_MAX_RANK + g] = sum;
+            }
+            T* tmp = cur; cur = nxt; nxt = tmp;
+        }
+        __syncthreads();
+        for (int l0 = 0; l0 < Kl; l0 += ALS_LB) {
+            const int lb = min(ALS_LB, Kl - l0);
+            // S[l][(beta, alpha)] = sum_g M[beta][g] Z_last[g, l0 + l, alpha]
+            for (int e = tid; e < ALS_LB * C; e += blockDim.x) {
+                const int l = e / C, c = e % C;
+                T sum = T(0);
+                if (l < lb) {
+                    const int be = c / Rn, al = c % Rn;
+                    for (int g = 0; g < Rl; ++g)
+                        sum = fma(cur[be * RTR_MAX_RANK + g], reinterpret_cast<const T*>(a.Z[ml])[((int64_t)g * Kl + l0 + l) * Rn + al], sum);
+                }
+                S[e] = sum;
+            }
+            for (int e = tid; e < ALS_LB * Kn; e += blockDim.x) {
+                const int l = e / Kn, i = e % Kn;
+                Pv[e] = (l < lb) ? P[base + (int64_t)(l0 + l) * a.stride[ml] + (int64_t)i * a.stride[n]] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < ALS_MAXACC; ++q) {
+                const int e = tid + q * 256;
+                if (e < nout) {
+                    const int i = e / C, c = e % C;
+                    T sum = acc[q];
+#pragma unroll 4
+                    for (int l = 0; l < ALS_LB; ++l) sum = fma(Pv[l * Kn + i], S[l * C + c], sum);
+                    acc[q] = sum;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < ALS_MAXACC; ++q) {
+        const int e = tid + q * 256;
+        if (e < nout) a.partial[(int64_t)blockIdx.x * nout + e] = (double)acc[q];
+    }
+}
+
+// W[e] = sum of the CTA partials (one warp per output, fixed order)
+__global__ void als_reduce_kernel(const double* __restrict__ partial, int nparts, int count, double* __restrict__ W) {
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= count) return;
+    double s = 0.0;
+    for (int q = lane; q < nparts; q += 32) s += partial[(int64_t)q * count + e];
+    s = rtr::warp_sum(s);
+    if (lane == 0) W[e] = s;
+}
+
+// Mprod = E_{s} E_{s+1} ... (cyclic, cnt factors), one CTA per output row:
+// the row is carried through the chain in shared memory (float64).
+struct GramChainArgs {
+    const double* E[RTR_MAXN];
+    int R[RTR_MAXN];
+    int N, start, cnt;
+    double* out;
+    int reindex, Rb, Rn;      // reindex: write G[(b, a), (b', a')] = M[(b, b'), (a, a')]
+};
+__global__ void __launch_bounds__(256) gram_chain_kernel(const GramChainArgs g) {
+    __shared__ double v0[256], v1[256];
+    const int r = blockIdx.x;
+    int m = g.start % g.N;
+    int len = g.R[(m + 1) % g.N] * g.R[(m + 1) % g.N];
+    for (int j = threadIdx.x; j < len; j += blockDim.x) v0[j] = g.E[m][(int64_t)r * len + j];
+    double* cur = v0;
+    double* nxt = v1;
+    for (int t = 1; t < g.cnt; ++t) {
+        __syncthreads();
+        m = (g.start + t) % g.N;
+        const int cols = g.R[(m + 1) % g.N] * g.R[(m + 1) % g.N];
+        for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+            double s = 0.0;
+            for (int l = 0; l < len; ++l) s += cur[l] * g.E[m][(int64_t)l * cols + j];
+            nxt[j] = s;
+        }
+        double* tmp = cur; cur = nxt; nxt = tmp;
+        len = cols;
+    }
+    __syncthreads();
+    if (g.reindex) {
+        const int C = g.Rb * g.Rn;
+        const int be = r / g.Rb, be2 = r % g.Rb;
+        for (int j = threadIdx.x; j < len; j += blockDim.x) {
+            const int al = j / g.Rn, al2 = j % g.Rn;
+            g.out[(int64_t)(be * g.Rn + al) * C + be2 * g.Rn + al2] = cur[j];
+        }
+    } else {
+        for (int j = threadIdx.x; j < len; j += blockDim.x) g.out[(int64_t)r * len + j] = cur[j];
+    }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+// single CTA: refresh the float32 shadow if the slow path ran, then clear its flag
+__global__ void shadow_if_slow_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n,
+                                      int* __restrict__ slow_ran) {
+    __shared__ int ran;
+    if (threadIdx.x == 0) ran = *(volatile int*)slow_ran;
+    __syncthreads();
+    if (!ran) return;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) b[e] = (float)a[e];
+    __syncthreads();
+    if (threadIdx.x == 0) *slow_ran = 0;
+}
+
+// G[c][c'] of the update of core n from the transfer product (reindexing
+// (beta, beta'), (alpha, alpha') -> (beta, alpha), (beta', alpha')).
+__device__ __forceinline__ double gram_at(const double* __restrict__ Mprod, int Rn, int Rn1, int c, int c2) {
+    const int be = c / Rn, al = c % Rn, be2 = c2 / Rn, al2 = c2 % Rn;
+    return Mprod[((int64_t)be * Rn1 + be2) * (Rn * Rn) + al * Rn + al2];
+}
+
+constexpr int SOLVE_MAXC = 160;       // R_n R_{n+1} <= 144
+
+// Fast path of the core update: one CTA per slice i of mode n solves
+// G z_i = w_i by mixed-precision iterative refinement (Wilkinson; Moler
+// 1967).  G (float64, already in (beta, alpha) order) is equilibrated,
+// D G D with D = diag(G)^-1/2 in float32, factored by Cholesky in float32 and
+// L^-1 is formed explicitly (one warp per column); each refinement step forms
+// the residual w - G z in float64 and adds D L^-T L^-1 D r (two parallel
+// triangular products), until ||dz|| <= sqrt(tol2) ||z|| or the corrections
+// stop shrinking (the float64 rounding floor).  1024 threads: the factorisation
+// is a chain of C barrier-separated steps whose latency needs many warps.
+// If a float32 pivot is not positive the CTA raises *need_slow and the
+// float64 slow path takes over.  Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
+constexpr int SOLVE_THREADS = 1024;
+
+__global__ void __launch_bounds__(SOLVE_THREADS) als_solve_fast_kernel(
+    const double* __restrict__ G, int Rn, int Rn1, int In, const double* __restrict__ W,
+    double* __restrict__ Zn, float* __restrict__ Znf, double* __restrict__ zw_out, int* __restrict__ need_slow,
+    int* __restrict__ flags, double tol2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = Rn * Rn1;
+    const int ld = C + 1;
+    const size_t msz = ((size_t)C * ld + 3) & ~(size_t)3;    // keeps every region 16-byte aligned
+    float* Ls = reinterpret_cast<float*>(smem_raw);           // C x ld: Cholesky factor
+    float* Li = Ls + msz;                                     // C x ld: L^-1 (lower)
+    double* z = reinterpret_cast<double*>(Li + msz);
+    double* w = z + C;
+    double* r = w + C;
+    float* sc = reinterpret_cast<float*>(r + C);
+    float* rs = sc + C;
+    float* ys = rs + C;
+    __shared__ double red[32];
+    __shared__ int conv;
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int tx = tid & 15, ty = tid >> 4, nty = blockDim.x >> 4;
+#ifdef RTR_DEBUG_ITERS
+    long long t_0 = clock64(), t_1 = 0, t_2 = 0, t_3 = 0;
+#endif
+    (void)flags;
+
+    for (int c = tid; c < C; c += blockDim.x) {
+        const float d = (float)G[(int64_t)c * C + c];
+        sc[c] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 0.f;
+        w[c] = W[(int64_t)i * C + c];
+        z[c] = 0.0;
+    }
+    __syncthreads();
+    int ok = 1;
+    for (int c = tid; c < C; c += blockDim.x) if (!(sc[c] > 0.f)) ok = 0;
+    for (int c = ty; c < C; c += nty) {
+        const double* grow = G + (int64_t)c * C;
+        for (int c2 = tx; c2 < C; c2 += 16) {
+            const float gs = (float)grow[c2] * sc[c] * sc[c2];
+            if (!isfinite(gs)) ok = 0;
+            Ls[c * ld + c2] = gs;
+        }
+    }
+    ok = __syncthreads_and(ok);
+#ifdef RTR_DEBUG_ITERS
+    t_1 = clock64();
+#endif
+    if (ok) ok = rtr::block_cholesky<float>(Ls, C, ld) ? 1 : 0;
+#ifdef RTR_DEBUG_ITERS
+    t_2 = clock64();
+#endif
+    if (!ok) {
+        if (tid == 0) atomicExch(need_slow, 1);
+        return;
+    }
+    // L^-1, column j by warp j mod nwarp: forward substitution of e_j, vector over lanes
+    for (int j = warp; j < C; j += nwarp) {
+        float y[SOLVE_MAXC / 32];
+#pragma unroll
+        for (int t = 0; t < SOLVE_MAXC / 32; ++t) y[t] = (lane + 32 * t == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int ks = 0; ks < SOLVE_MAXC / 32; ++ks) {
+            for (int kk = 0; kk < 32; ++kk) {
+                const int k = ks * 32 + kk;
+                if (k >= C) break;
+                if (k < j) continue;
+                const float yk = __shfl_sync(0xffffffffu, y[ks], kk) / Ls[k * ld + k];
+                if (lane == kk) y[ks] = yk;
+#pragma unroll
+                for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
+                    const int m = lane + 32 * t;
+                    if (m > k && m < C) y[t] -= Ls[m * ld + k] * yk;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
+            const int m = lane + 32 * t;
+            if (m < C) Li[m * ld + j] = (m >= j) ? y[t] : 0.f;
+        }
+    }
+    __syncthreads();
+#ifdef RTR_DEBUG_ITERS
+    t_3 = clock64();
+#endif
+    double dz2_prev = 0.0;
+    int used = 0;
+    for (int it = 0; it < 12; ++it) {
+        used = it + 1;
+        // r = w - G z in float64: four lanes per row (adjacent), rows in L2-cached G
+        for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
+            const int e = e0 + lane;
+            const int c2 = e >> 2, q = e & 3;
+            double acc = 0.0;
+            if (c2 < C) {
+                const double* grow = G + (int64_t)c2 * C;
+                for (int c = q; c < C; c += 4) acc += z[c] * grow[c];
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (c2 < C && q == 0) rs[c2] = (float)(w[c2] - acc) * sc[c2];
+        }
+        __syncthreads();
+        // ys = L^-1 rs  (row c over lanes of a quad)
+        for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
+            const int e = e0 + lane;
+            const int c = e >> 2, q = e & 3;
+            float acc = 0.f;
+            if (c < C)
+                for (int b = q; b <= c; b += 4) acc = fmaf(Li[c * ld + b], rs[b], acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (c < C && q == 0) ys[c] = acc;
+        }
+        __syncthreads();
+        // dz = D L^-T ys
+        double dz2 = 0.0, z2 = 0.0;
+        for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
+            const int e = e0 + lane;
+            const int c = e >> 2, q = e & 3;
+            float acc = 0.f;
+            if (c < C)
+                for (int b = c + q; b < C; b += 4) acc = fmaf(Li[b * ld + c], ys[b], acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (c < C && q == 0) {
+                const double dz = (double)(acc * sc[c]);
+                const double zn = z[c] + dz;
+                z[c] = zn;
+                dz2 += dz * dz;
+                z2 += zn * zn;
+            }
+        }
+        dz2 = rtr::block_sum(dz2, red);
+        z2 = rtr::block_sum(z2, red);
+        if (tid == 0) conv = (dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25 * dz2_prev)) ? 1 : 0;
+        dz2_prev = dz2;
+        __syncthreads();
+        if (conv) break;
+    }
+#ifdef RTR_DEBUG_ITERS
+    if (tid == 0 && blockIdx.x == 0)
+        printf("refine iters %d C=%d build %lld chol %lld linv %lld iters %lld clk\n", used, C, t_1 - t_0,
+               t_2 - t_1, t_3 - t_2, clock64() - t_3);
+#else
+    (void)used;
+#endif
+    double zw = 0.0;
+    for (int c = tid; c < C; c += blockDim.x) {
+        const int be = c / Rn, al = c % Rn;
+        const int64_t o = ((int64_t)al * In + i) * Rn1 + be;
+        Zn[o] = z[c];
+        if (Znf) Znf[o] = (float)z[c];
+        zw += z[c] * w[c];
+    }
+    zw = rtr::block_sum(zw, red);
+    if (tid == 0) zw_out[i] = zw;
+}
+
+// ||P - TR(Z)|| after the last update of a sweep: sqrt(||P||^2 - sum_i z_i . w_i)
+// (at the least-squares solution ||TR(Z)||^2 = sum_i z_i . w_i).
+__global__ void als_err_kernel(const double* __restrict__ zw, int In, const double* __restrict__ normP2,
+                               double* __restrict__ err_out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < In; ++i) s += zw[i];
+        *err_out = sqrt(fmax(*normP2 - s, 0.0));
+    }
+}
+
+// Slow path (runs only if the fast path raised *need_slow): float64
+// Cholesky of G in shared memory and direct solves, or, if G is not SPD in
+// float64 either, the eigen-pseudo-inverse with cutoff 1e-13 lambda_max
+// (Jacobi eigendecomposition in global scratch).
+__global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __restrict__ Mprod, int Rn, int Rn1,
+                                                             int In, const double* __restrict__ W,
+                                                             double* __restrict__ Wz, double* __restrict__ Zn,
+                                                             double* __restrict__ zw_out, double* __restrict__ jac_ws,
+                                                             int* __restrict__ need_slow, int* __restrict__ flags,
+                                                             int reset) {
+    if (*(volatile int*)need_slow == 0) return;
     extern __shared__ __align__(16) double Gs[];
     const int C = Rn * Rn1;
     const int ld = C + 1;
@@ -97,7 +500,7 @@ __global__ void __launch_bounds__(512) als_solve_kernel(const double* __restrict
     for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
         const int c = e / C, c2 = e % C;
         const int be = c / Rn, al = c % Rn, be2 = c2 / Rn, al2 = c2 % Rn;
-        Gs[c * ld + c2] = Mprod[((int64_t)be * Rn1 + be2) * (Rn * Rn) + al * Rn + al2];
+        Gs[c * ld + c2] = Mprod[(int64_t)c * C + c2]; (void)be; (void)al; (void)be2; (void)al2;
     }
     for (int e = threadIdx.x; e < In * C; e += blockDim.x) Wz[e] = W[e];
     __syncthreads();
@@ -120,7 +523,7 @@ __global__ void __launch_bounds__(512) als_solve_kernel(const double* __restrict
         for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
             const int c = e / C, c2 = e % C;
             const int be = c / Rn, al = c % Rn, be2 = c2 / Rn, al2 = c2 % Rn;
-            Aj[e] = Mprod[((int64_t)be * Rn1 + be2) * (Rn * Rn) + al * Rn + al2];
+            Aj[e] = Mprod[(int64_t)c * C + c2]; (void)be; (void)al; (void)be2; (void)al2;
         }
         __syncthreads();
         rtr::block_jacobi_eig(Aj, V, C, C, pairs, cs, 40);
@@ -145,16 +548,19 @@ __global__ void __launch_bounds__(512) als_solve_kernel(const double* __restrict
             __syncthreads();
         }
     }
-    double zw = 0.0;
     for (int e = threadIdx.x; e < In * C; e += blockDim.x) {
         const int i = e / C, c = e % C;
         const int be = c / Rn, al = c % Rn;
-        const double z = Wz[e];
-        zw += z * W[e];
-        Zn[((int64_t)al * In + i) * Rn1 + be] = z;
+        Zn[((int64_t)al * In + i) * Rn1 + be] = Wz[e];
     }
-    zw = rtr::block_sum(zw, red);
-    if (err_out && threadIdx.x == 0) *err_out = sqrt(fmax(*normP2 - zw, 0.0));
+    __syncthreads();
+    for (int i = threadIdx.x; i < In; i += blockDim.x) {
+        double zw = 0.0;
+        for (int c = 0; c < C; ++c) zw += Wz[(int64_t)i * C + c] * W[(int64_t)i * C + c];
+        zw_out[i] = zw;
+    }
+    __syncthreads();
+    if (reset && threadIdx.x == 0) *need_slow = 0;    // else the shadow refresh clears it
 }
 
 // Default start: entry e of core n is the fp64 table value at field e % 20 of
@@ -305,14 +711,22 @@ T* build_chain(int N, const int64_t* dims, const int* R, const double* const* Z,
     int which = 0;
     int64_t Jp = 1;
     const int Rfirst = R[start % N];
-    for (int t = 0; t < count; ++t) {
+    const double* zfirst = nullptr;
+    int t0 = 0;
+    if (count >= 2) {          // fold the first core into the first product
+        zfirst = Z[start % N];
+        Jp = dims[start % N];
+        t0 = 1;
+    }
+    for (int t = t0; t < count; ++t) {
         const int m = (start + t) % N;
         const int Km = (int)dims[m];
         const int Rc = R[m], Rd = R[(m + 1) % N];
         T* out = bufs[which];
         const int fin = (t == count - 1) ? final_tr : 0;
         const int64_t total = Jp * Km * Rfirst * Rd;
-        subchain_step_kernel<T><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out, fin, Aa, Bb);
+        subchain_step_kernel<T><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out, fin, Aa, Bb,
+                                                                t == t0 ? zfirst : nullptr);
         rtr_count_launch();
         if (cudaGetLastError() != cudaSuccess) { *status = RTR_ECUDA; return nullptr; }
         cur = out;
@@ -336,6 +750,8 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     double* W = ws + (RTR_MAXN + 2) * ESZ;
     double* Wz = W + p->als_wmax;
     double* jac = Wz + p->als_wmax;              // 2 * 144^2 for the pinv fallback
+    double* zw = jac + 2 * 144 * 144;            // z_i . w_i per slice (max K_n)
+    int* need_slow = reinterpret_cast<int*>(p->scal + 24);
     double* normP2 = p->scal + 1;
     double* normTR2 = p->scal + 2;
 
@@ -357,7 +773,8 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             const int m = (start + t) % N;
             const int k = p->R[m] * p->R[m];
             const int cols = p->R[(m + 1) % N] * p->R[(m + 1) % N];
-            matmul_f64_kernel<<<grid_for((int64_t)rows * cols, 64), 64, 0, s>>>(cur, E[m], Mp[which], rows, k, cols);
+            matmul_f64_kernel<<<dim3((unsigned)rtr_ceil_div(cols, 8), (unsigned)rtr_ceil_div(rows, 8)), 64, 0, s>>>(
+                cur, E[m], Mp[which], rows, k, cols);
             RTR_LAUNCH_CHECK("matmul_f64_kernel");
             cur = Mp[which];
             which ^= 1;
@@ -383,31 +800,99 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             RTR_LAUNCH_CHECK("scale_cores_kernel");
         }
     }
+    // transfer matrices of the start; the transfer of each updated core and
+    // the Gram chain of the next update then run on the plan's side stream,
+    // concurrently with the contraction on the caller's stream
     for (int n = 0; n < N; ++n) if ((st = transfer(n))) return st;
 
-    T* sb0 = (T*)p->sub_ws[0];
-    T* sb1 = (T*)p->sub_ws[1];
+    // compute-type core copies read by the contraction (float32 shadows for
+    // the FP32/BF16 plans; the FP64 plan reads its cores directly)
+    const void* Zt[RTR_MAXN];
+    float* Zf[RTR_MAXN] = {};
+    if (!is_f64) {
+        float* zf = reinterpret_cast<float*>(zw + p->als_maxK);
+        for (int n = 0; n < N; ++n) {
+            const int64_t cnt = (int64_t)p->R[n] * Kd[n] * p->R[(n + 1) % N];
+            Zf[n] = zf;
+            zf += (cnt + 3) & ~(int64_t)3;
+            to_f32_kernel<<<grid_for(cnt), 256, 0, s>>>(Z[n], Zf[n], cnt);
+            RTR_LAUNCH_CHECK("to_f32_kernel");
+            Zt[n] = Zf[n];
+        }
+    } else {
+        for (int n = 0; n < N; ++n) Zt[n] = Z[n];
+    }
+    cudaStream_t side = p->side;
     for (int sweep = 0; sweep < p->params.sweeps; ++sweep) {
         for (int n = 0; n < N; ++n) {
             const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
             const int C = Rn * Rn1;
             int64_t A, I, B;
             rtr_mode_view(N, Kd, n, &A, &I, &B);
-            // subchain S (rows a*B + b, columns (beta, alpha))
-            T* S = build_chain<T>(N, Kd, p->R, Z, n + 1, N - 1, sb0, sb1, 1, A, B, s, &st);
-            if (!S) return rtr_set_error(RTR_ECUDA, "subchain kernel launch failed");
-            ContractArgs ca{};
-            ca.X = P; ca.A = A; ca.I = I; ca.B = B; ca.C = C;
-            ca.gen = 0; ca.M = S; ca.ldm = C; ca.Y = W; ca.norm_out = nullptr;
-            if ((st = launch_contract(p, is_f64, ca, s))) return st;
-            double* Mprod = nullptr;
-            if ((st = eprod(n + 1, N - 1, &Mprod))) return st;
-            const size_t smem = sizeof(double) * (size_t)C * (C + 1);
-            RTR_CUDA(cudaFuncSetAttribute(als_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            double* eo = (err && n == N - 1) ? err + sweep : nullptr;
-            als_solve_kernel<<<1, 512, smem, s>>>(Mprod, Rn, Rn1, (int)I, W, Wz, Z[n], normP2, eo, jac, p->flags);
-            RTR_LAUNCH_CHECK("als_solve_kernel");
-            if ((st = transfer(n))) return st;
+            // ---- side stream: E of the core updated last, then G = E_{n+1} ... E_{n-1}
+            RTR_CUDA(cudaEventRecord(p->ev[0], s));
+            RTR_CUDA(cudaStreamWaitEvent(side, p->ev[0], 0));
+            if (sweep > 0 || n > 0) {
+                const int m = (n + N - 1) % N;
+                const int Ra = p->R[m], Rb = p->R[(m + 1) % N];
+                transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb), 256, 0, side>>>(Z[m], Ra, (int)Kd[m], Rb, E[m]);
+                RTR_LAUNCH_CHECK("transfer_kernel");
+            }
+            GramChainArgs gc{};
+            for (int m = 0; m < N; ++m) { gc.E[m] = E[m]; gc.R[m] = p->R[m]; }
+            gc.N = N; gc.start = n + 1; gc.cnt = N - 1; gc.out = Mp[0];
+            gc.reindex = 1; gc.Rb = Rn1; gc.Rn = Rn;
+            gram_chain_kernel<<<(unsigned)(Rn1 * Rn1), 256, 0, side>>>(gc);
+            RTR_LAUNCH_CHECK("gram_chain_kernel");
+            RTR_CUDA(cudaEventRecord(p->ev[1], side));
+            // ---- caller's stream: W = P_<n> S, subchain generated in the contraction
+            AlsContractArgs ca{};
+            ca.P = P; ca.N = N; ca.n = n; ca.partial = p->partial;
+            {
+                int64_t st_ = 1;
+                for (int m = N - 1; m >= 0; --m) { ca.stride[m] = st_; st_ *= Kd[m]; }
+            }
+            for (int m = 0; m < N; ++m) { ca.Z[m] = Zt[m]; ca.K[m] = Kd[m]; ca.R[m] = p->R[m]; }
+            for (int t = 0; t < N; ++t) ca.cyc[t] = (n + t) % N;
+            ca.Jpre = 1;
+            for (int t = 1; t <= N - 2; ++t) ca.Jpre *= Kd[ca.cyc[t]];
+            const int nout = (int)I * C;
+            if (nout > 256 * ALS_MAXACC) return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: K_n R_n R_{n+1} > 10240");
+            int64_t gx = std::min<int64_t>(ca.Jpre, 4 * (int64_t)p->num_sms);
+            gx = std::min<int64_t>(gx, (int64_t)(p->partial_elems / nout));
+            const size_t csmem = sizeof(T) * (2 * (size_t)Rn1 * RTR_MAX_RANK + (size_t)ALS_LB * C + (size_t)ALS_LB * I);
+            als_contract_kernel<T><<<(unsigned)gx, 256, csmem, s>>>(ca);
+            RTR_LAUNCH_CHECK("als_contract_kernel");
+            als_reduce_kernel<<<(unsigned)rtr_ceil_div((int64_t)nout * 32, 256), 256, 0, s>>>(p->partial, (int)gx, nout, W);
+            RTR_LAUNCH_CHECK("als_reduce_kernel");
+            // ---- join, then solve G z_i = w_i for every slice
+            RTR_CUDA(cudaStreamWaitEvent(s, p->ev[1], 0));
+            double* G = Mp[0];
+            const size_t fsmem = 2 * sizeof(float) * ((((size_t)C * (C + 1)) + 3) & ~(size_t)3) +
+                                 3 * sizeof(double) * C + 3 * sizeof(float) * C;
+            RTR_CUDA(cudaFuncSetAttribute(als_solve_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)fsmem));
+            // refinement target: float64 accuracy for FP64 plans, 1e-9 relative otherwise
+            const double tol2 = is_f64 ? 1e-28 : 1e-18;
+            als_solve_fast_kernel<<<(unsigned)I, SOLVE_THREADS, fsmem, s>>>(G, Rn, Rn1, (int)I, W, Z[n], Zf[n], zw,
+                                                                           need_slow, p->flags, tol2);
+            RTR_LAUNCH_CHECK("als_solve_fast_kernel");
+            const size_t ssmem = sizeof(double) * (size_t)C * (C + 1);
+            RTR_CUDA(cudaFuncSetAttribute(als_solve_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)ssmem));
+            als_solve_slow_kernel<<<1, 512, ssmem, s>>>(G, Rn, Rn1, (int)I, W, Wz, Z[n], zw, jac, need_slow,
+                                                        p->flags, is_f64);
+            RTR_LAUNCH_CHECK("als_solve_slow_kernel");
+            if (!is_f64) {
+                const int64_t cnt = (int64_t)Rn * I * Rn1;
+                // the slow path (rare) writes only float64 cores: refresh the shadow
+                shadow_if_slow_kernel<<<1, 256, 0, s>>>(Z[n], Zf[n], cnt, need_slow);
+                RTR_LAUNCH_CHECK("shadow_if_slow_kernel");
+            }
+            if (err && n == N - 1) {
+                als_err_kernel<<<1, 32, 0, s>>>(zw, (int)I, normP2, err + sweep);
+                RTR_LAUNCH_CHECK("als_err_kernel");
+            }
         }
     }
     return RTR_OK;

@@ -143,16 +143,21 @@ __global__ void __launch_bounds__(NT) contract_kernel(
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nparts, int64_t count,
                                        double* __restrict__ Y, const double* __restrict__ normp,
                                        int nnorm, double* __restrict__ norm_out) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // one warp per output: lanes stride over the partials, then a fixed-order
+    // butterfly; the result does not depend on timing
+    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (e < count) {
         double s = 0.0;
-        for (int p = 0; p < nparts; ++p) s += partial[p * count + e];
-        Y[e] = s;
+        for (int p = lane; p < nparts; p += 32) s += partial[p * count + e];
+        s = rtr::warp_sum(s);
+        if (lane == 0) Y[e] = s;
     }
-    if (norm_out && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (norm_out && blockIdx.x == 0 && threadIdx.x < 32) {
         double s = 0.0;
-        for (int p = 0; p < nnorm; ++p) s += normp[p];
-        *norm_out = s;
+        for (int p = lane; p < nnorm; p += 32) s += normp[p];
+        s = rtr::warp_sum(s);
+        if (lane == 0) *norm_out = s;
     }
 }
 
@@ -191,6 +196,9 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
     if (a.B == 1) nchunks = rtr_ceil_div(a.A, RC);
     else { nbc = rtr_ceil_div(a.B, RC); nchunks = a.A * nbc; }
     int64_t gx = std::max<int64_t>(1, (int64_t)occ * p->num_sms / sh.gy);
+    // a stored operand (the TR-ALS contraction) is small: give every CTA a few
+    // chunks so that the partial reduction stays short
+    if (!GEN) gx = std::min<int64_t>(gx, std::max<int64_t>(1, nchunks / 4));
     gx = std::min<int64_t>(gx, nchunks);
     gx = std::max<int64_t>(gx, 1);
     const int64_t need = gx * a.I * a.C;
@@ -208,7 +216,7 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
                                 want_norm ? p->normx_part : nullptr);
     RTR_LAUNCH_CHECK("contract_kernel");
     const int64_t count = a.I * a.C;
-    reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count, 256), 256, 0, s>>>(
+    reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
         p->partial, (int)gx, count, a.Y, p->normx_part, (int)(gx * sh.gy), want_norm ? a.norm_out : nullptr);
     RTR_LAUNCH_CHECK("reduce_partials_kernel");
     return RTR_OK;
@@ -316,7 +324,7 @@ int launch_noalloc(const NoAllocDevice& d, const ContractArgs& a, const Shape& s
                                 a.mode, (const T*)a.table, nullptr, 0, d.scratch, nullptr);
     RTR_LAUNCH_CHECK("contract_kernel (no-alloc)");
     const int64_t count = a.I * a.C;
-    reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count, 256), 256, 0, s>>>(d.scratch, (int)gx, count, a.Y,
+    reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(d.scratch, (int)gx, count, a.Y,
                                                                                 nullptr, 0, nullptr);
     RTR_LAUNCH_CHECK("reduce_partials_kernel (no-alloc)");
     return RTR_OK;

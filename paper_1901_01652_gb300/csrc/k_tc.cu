@@ -1,15 +1,635 @@
-// tcgen05 (5th-generation tensor core) sketch and mode product, BF16 hi+lo split.
+// tcgen05 (5th-generation tensor core) Gaussian sketch, Algorithm 1 step 5:
+//     Y_n[i, k] = sum_r X_(n)[i, r] Omega_n[r, k]
+// with X float32 in HBM split in registers into bfloat16 hi + lo
+// (x ~= hi + lo to ~2^-17 relative), Omega_n exactly bfloat16 (the
+// bfloat16-rounded quantile table), FP32 accumulation in TMEM:
+//     D[i, k] += A_hi[i, r] B[r, k] + A_lo[i, r] B[r, k].
+//
+// CTA = 11 warps, one CTA per SM (smem-bound), persistent over chunks of 64
+// consecutive r (grid-stride):
+//   warps 0-7  converters: vectorised global loads of X, hi/lo split, stores
+//              into 128B-swizzled K-major tiles; then the epilogue (TMEM ->
+//              float64 partials)
+//   warps 8-9  Omega generators: Philox4x64-10 + table lookup into the B tile
+//   warp 10    one elected lane issues tcgen05.mma and commits stage releases
+// A ring of S stages (A_hi, A_lo, B per stage) is handed over with mbarriers;
+// every wait is bounded (tc_common.cuh) and raises RTR_FLAG_TIMEOUT.
+// The accumulators D (one 128 x N block per 128-row M tile) live in TMEM.
+#include <algorithm>
 #include "rtr_internal.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+using namespace rtr::tc;
+
+constexpr int CONV_WARPS = 8;
+constexpr int RNG_WARPS = 2;
+constexpr int MMA_WARP = CONV_WARPS + RNG_WARPS;
+constexpr int NTHREADS = (CONV_WARPS + RNG_WARPS + 1) * 32;
+constexpr int CONV_THREADS = CONV_WARPS * 32;
+constexpr int RNG_THREADS = RNG_WARPS * 32;
+constexpr int KC = 64;                       // reduction values per chunk (one 128-byte bf16 row)
+constexpr uint32_t MTILE_BYTES = 128 * 128;  // 128 rows x 128 bytes
+
+struct SketchTCArgs {
+    const float* X;
+    int64_t A, B;
+    int I, K, N, MT, rows_cta, S;
+    int64_t nchunks, nbc;
+    uint64_t seed;
+    int mode;
+    int vec;                      // 1: 16-byte vector loads are legal
+    const uint16_t* tab;          // bfloat16 table (global)
+    double* partial;              // [gridDim.x][I][K]
+    double* normp;                // [gridDim.y * gridDim.x] or null
+    int* flags;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    uint8_t* sm = smem_raw + pad;
+    const uint32_t a_bytes = (uint32_t)p.MT * MTILE_BYTES;
+    const uint32_t b_bytes = (uint32_t)p.N * 128u;
+    const uint32_t stage_bytes = 2 * a_bytes + b_bytes;
+    const int S = p.S;
+    uint16_t* tab = reinterpret_cast<uint16_t*>(sm + S * stage_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tab + 4096);
+    uint64_t* fullA = bars;
+    uint64_t* fullB = bars + S;
+    uint64_t* empty = bars + 2 * S;
+    uint64_t* accf = bars + 3 * S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    double* nred = reinterpret_cast<double*>(bars + 3 * S + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ncols = (uint32_t)(p.MT * p.N);
+
+    // ---- set-up: zero all operand tiles (padding rows/columns stay zero), table, barriers, TMEM
+    {
+        const uint32_t base = smem_u32(sm);
+        for (uint32_t off = tid * 16u; off < (uint32_t)S * stage_bytes; off += NTHREADS * 16u)
+            asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(base + off), "r"(0) : "memory");
+        for (int j = tid; j < 4096; j += NTHREADS) tab[j] = p.tab[j];
+        if (tid == 0) {
+            for (int s = 0; s < S; ++s) {
+                mbar_init(&fullA[s], CONV_THREADS);
+                mbar_init(&fullB[s], RNG_THREADS);
+                mbar_init(&empty[s], 1);
+            }
+            mbar_init(accf, 1);
+            *abort = 0;
+            mbar_fence_init();
+        }
+        if (warp == MMA_WARP) tmem_alloc(tmem_slot, ncols);
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    const uint32_t tmem = *tmem_slot;
+    const int rbeg = blockIdx.y * p.rows_cta;
+    const int rows_valid = min(p.rows_cta, p.I - rbeg);
+    const int64_t nloc = (blockIdx.x < p.nchunks) ? (p.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t stage0 = smem_u32(sm);
+    double nsum = 0.0;
+
+    if (warp < CONV_WARPS) {
+        // ================================================================ converters
+        const int ct = tid;
+        for (int64_t t = 0; t < nloc; ++t) {
+            const int64_t ch = blockIdx.x + t * gridDim.x;
+            const int s = (int)(t % S);
+            const uint32_t u = (uint32_t)(t / S);
+            if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
+            const uint32_t hi_base = stage0 + s * stage_bytes;
+            const uint32_t lo_base = hi_base + a_bytes;
+            float csum = 0.f;
+            if (p.B > 1) {
+                const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * KC;
+                const int len = (int)min((int64_t)KC, p.B - b0);
+                const float* xrow0 = p.X + ((int64_t)a * p.I + rbeg) * p.B + b0;
+                if (p.vec && len == KC) {
+                    // piece = (row, 16-byte column group c4): 16 pieces per row
+                    const int npieces = rows_valid * 16;
+                    float4 v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int pc = ct + CONV_THREADS * j;
+                        if (pc < npieces)
+                            v[j] = __ldg(reinterpret_cast<const float4*>(xrow0 + (int64_t)(pc >> 4) * p.B) + (pc & 15));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int pc = ct + CONV_THREADS * j;
+                        if (pc < npieces) {
+                            const int row = pc >> 4, c4 = pc & 15;
+                            uint32_t h0, l0, h1, l1;
+                            split2(v[j].x, v[j].y, h0, l0);
+                            split2(v[j].z, v[j].w, h1, l1);
+                            csum += v[j].x * v[j].x + v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
+                            const uint32_t off = (uint32_t)(row >> 7) * MTILE_BYTES + sw128_off(row & 127, 4 * c4);
+                            st_shared_v2(hi_base + off, h0, h1);
+                            st_shared_v2(lo_base + off, l0, l1);
+                        }
+                    }
+                } else {
+                    for (int e = ct; e < rows_valid * (KC / 2); e += CONV_THREADS) {
+                        const int row = e / (KC / 2), kp = e % (KC / 2);
+                        const int k0 = 2 * kp;
+                        const float x0 = (k0 < len) ? xrow0[(int64_t)row * p.B + k0] : 0.f;
+                        const float x1 = (k0 + 1 < len) ? xrow0[(int64_t)row * p.B + k0 + 1] : 0.f;
+                        uint32_t h, l;
+                        split2(x0, x1, h, l);
+                        csum += x0 * x0 + x1 * x1;
+                        const uint32_t off = (uint32_t)(row >> 7) * MTILE_BYTES + sw128_off(row & 127, k0);
+                        st_shared_u32(hi_base + off, h);
+                        st_shared_u32(lo_base + off, l);
+                    }
+                }
+            } else {
+                // last mode: r = a; X[a, i] is contiguous along i, so the tile is
+                // transposed on the way in: item = (pair q of r values, quad u of rows)
+                const int64_t a0 = ch * KC;
+                const int len = (int)min((int64_t)KC, p.A - a0);
+                const float* xb = p.X + a0 * p.I + rbeg;
+                if (p.vec) {
+                    const int nitems = (rows_valid >> 2) * 32;
+                    for (int it0 = 0; it0 < nitems; it0 += CONV_THREADS * 4) {
+                        float4 x0[4], x1[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int it = it0 + ct + CONV_THREADS * j;
+                            const int q = it & 31, u4 = it >> 5;
+                            x0[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            x1[j] = x0[j];
+                            if (it < nitems) {
+                                if (2 * q < len) x0[j] = __ldg(reinterpret_cast<const float4*>(xb + (int64_t)(2 * q) * p.I + 4 * u4));
+                                if (2 * q + 1 < len) x1[j] = __ldg(reinterpret_cast<const float4*>(xb + (int64_t)(2 * q + 1) * p.I + 4 * u4));
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int it = it0 + ct + CONV_THREADS * j;
+                            if (it >= nitems) continue;
+                            const int q = it & 31, u4 = it >> 5;
+                            const float a0v[4] = {x0[j].x, x0[j].y, x0[j].z, x0[j].w};
+                            const float a1v[4] = {x1[j].x, x1[j].y, x1[j].z, x1[j].w};
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                const int row = 4 * u4 + v;
+                                uint32_t h, l;
+                                split2(a0v[v], a1v[v], h, l);
+                                csum += a0v[v] * a0v[v] + a1v[v] * a1v[v];
+                                const uint32_t off = (uint32_t)(row >> 7) * MTILE_BYTES + sw128_off(row & 127, 2 * q);
+                                st_shared_u32(hi_base + off, h);
+                                st_shared_u32(lo_base + off, l);
+                            }
+                        }
+                    }
+                } else {
+                    for (int e = ct; e < rows_valid * (KC / 2); e += CONV_THREADS) {
+                        const int q = e % (KC / 2), row = e / (KC / 2);
+                        const float x0 = (2 * q < len) ? xb[(int64_t)(2 * q) * p.I + row] : 0.f;
+                        const float x1 = (2 * q + 1 < len) ? xb[(int64_t)(2 * q + 1) * p.I + row] : 0.f;
+                        uint32_t h, l;
+                        split2(x0, x1, h, l);
+                        csum += x0 * x0 + x1 * x1;
+                        const uint32_t off = (uint32_t)(row >> 7) * MTILE_BYTES + sw128_off(row & 127, 2 * q);
+                        st_shared_u32(hi_base + off, h);
+                        st_shared_u32(lo_base + off, l);
+                    }
+                }
+            }
+            nsum += (double)csum;
+            fence_proxy_async();
+            mbar_arrive(&fullA[s]);
+        }
+    } else if (warp < MMA_WARP) {
+        // ================================================================ Omega generators
+        const int kk = tid - CONV_THREADS;            // 0..63: the r column this thread fills
+        const int ncall = (p.K + 19) / 20;
+        for (int64_t t = 0; t < nloc; ++t) {
+            const int64_t ch = blockIdx.x + t * gridDim.x;
+            const int s = (int)(t % S);
+            const uint32_t u = (uint32_t)(t / S);
+            int64_t r0;
+            int len;
+            if (p.B > 1) {
+                const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * KC;
+                r0 = a * p.B + b0;
+                len = (int)min((int64_t)KC, p.B - b0);
+            } else {
+                r0 = ch * KC;
+                len = (int)min((int64_t)KC, p.A - r0);
+            }
+            if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
+            const uint32_t bt = stage0 + s * stage_bytes + 2 * a_bytes;
+            for (int cb = 0; cb < ncall; ++cb) {
+                uint64_t w[4] = {0, 0, 0, 0};
+                if (kk < len) rtr::omega_words(p.seed, p.mode, (uint64_t)(r0 + kk), (uint64_t)cb, w);
+#pragma unroll
+                for (int tt = 0; tt < 20; ++tt) {
+                    const int k = cb * 20 + tt;
+                    if (k < p.K) {
+                        const uint16_t val = (kk < len) ? tab[rtr::omega_field(w, tt)] : (uint16_t)0;
+                        st_shared_u16(bt + sw128_off(k, kk), val);
+                    }
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&fullB[s]);
+        }
+    } else {
+        // ================================================================ MMA issuer
+        const uint32_t idesc = idesc_bf16_f32(128, p.N);
+        for (int64_t t = 0; t < nloc; ++t) {
+            const int s = (int)(t % S);
+            const uint32_t u = (uint32_t)(t / S);
+            if (!mbar_wait(&fullA[s], u & 1, abort, p.flags)) break;
+            if (!mbar_wait(&fullB[s], u & 1, abort, p.flags)) break;
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t ahi = stage0 + s * stage_bytes, alo = ahi + a_bytes, bb = ahi + 2 * a_bytes;
+                for (int m = 0; m < p.MT; ++m) {
+                    const uint32_t d = tmem + (uint32_t)(m * p.N);
+#pragma unroll
+                    for (int j = 0; j < KC / 16; ++j) {
+                        const uint64_t bd = sdesc_sw128(bb + 32u * j);
+                        mma_bf16(d, sdesc_sw128(ahi + m * MTILE_BYTES + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
+                        mma_bf16(d, sdesc_sw128(alo + m * MTILE_BYTES + 32u * j), bd, idesc, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) mma_commit(accf);
+        __syncwarp();
+    }
+
+    // ==================================================================== epilogue
+    if (warp < CONV_WARPS) {
+        const int m = warp >> 2;
+        const bool have = nloc > 0;
+        bool ok = true;
+        if (have) {
+            ok = mbar_wait(accf, 0, abort, p.flags);
+            tc_fence_after();
+        }
+        if (m < p.MT) {
+            const int row = m * 128 + 32 * (warp & 3) + lane;
+            for (int c0 = 0; c0 < p.N; c0 += 32) {
+                float v[32];
+                if (have && ok) {
+                    tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(m * p.N + c0), v);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] = 0.f;
+                }
+                if (row < rows_valid) {
+                    double* dst = p.partial + ((int64_t)blockIdx.x * p.I + rbeg + row) * p.K;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k)
+                        if (c0 + k < p.K) dst[c0 + k] = (double)v[k];
+                }
+            }
+        }
+        if (p.normp) {
+            nsum = rtr::warp_sum(nsum);
+            if (lane == 0) nred[warp] = nsum;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (p.normp && tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < CONV_WARPS; ++w) s += nred[w];
+        p.normp[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+    if (warp == MMA_WARP) tmem_dealloc(tmem, ncols);
+}
+
+__global__ void tc_reduce_kernel(const double* __restrict__ partial, int nparts, int64_t count,
+                                       double* __restrict__ Y, const double* __restrict__ normp,
+                                       int nnorm, double* __restrict__ norm_out) {
+    // one warp per output: lanes stride over the partials, then a fixed-order
+    // butterfly; the result does not depend on timing
+    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e < count) {
+        double s = 0.0;
+        for (int p = lane; p < nparts; p += 32) s += partial[p * count + e];
+        s = rtr::warp_sum(s);
+        if (lane == 0) Y[e] = s;
+    }
+    if (norm_out && blockIdx.x == 0 && threadIdx.x < 32) {
+        double s = 0.0;
+        for (int p = lane; p < nnorm; p += 32) s += normp[p];
+        s = rtr::warp_sum(s);
+        if (lane == 0) *norm_out = s;
+    }
+}
+
+constexpr size_t SMEM_LIMIT = 232448;   // 227 KiB opt-in per CTA
+
+int sketch_geometry(int64_t I, int K, int* MT, int* N, int* S, size_t* smem) {
+    *N = (K <= 32) ? 32 : 64;
+    *MT = (I > 128) ? 2 : 1;
+    const size_t stage = 2 * (size_t)(*MT) * MTILE_BYTES + (size_t)(*N) * 128;
+    const size_t fixed = 8192 + 64 * 8 + 1024;
+    int s = (int)((SMEM_LIMIT - fixed) / stage);
+    s = std::min(s, 4);
+    if (s < 2) return 0;
+    *S = s;
+    *smem = fixed + (size_t)s * stage;
+    return 1;
+}
+
+}  // namespace
 
 size_t tc_ws_bytes(const rtr_plan* p) { (void)p; return 0; }
 
 int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s) {
-    (void)p; (void)X; (void)Y; (void)s;
-    return rtr_set_error(RTR_EUNSUPPORTED, "BF16 tensor-core sketch is not built yet");
+    bool norm_done = false;
+    for (int n = 0; n < p->N; ++n) {
+        if (!p->proj[n]) continue;
+        int64_t A, I, B;
+        rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
+        const int K = p->K[n];
+        int MT, N, S;
+        size_t smem;
+        if (!sketch_geometry(I, K, &MT, &N, &S, &smem))
+            return rtr_set_error(RTR_EUNSUPPORTED, "tensor-core sketch: no stage fits in shared memory");
+        SketchTCArgs a{};
+        a.X = X; a.A = A; a.B = B; a.I = (int)I; a.K = K; a.N = N; a.MT = MT; a.rows_cta = MT * 128; a.S = S;
+        if (B > 1) { a.nbc = rtr_ceil_div(B, KC); a.nchunks = A * a.nbc; }
+        else { a.nbc = 1; a.nchunks = rtr_ceil_div(A, KC); }
+        a.seed = p->params.seed; a.mode = n;
+        const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+        a.vec = aligned && ((B > 1) ? (B % 4 == 0) : (I % 4 == 0)) ? 1 : 0;
+        a.tab = p->tab_bf16;
+        a.flags = p->flags;
+        const int gy = (int)rtr_ceil_div(I, a.rows_cta);
+        int64_t gx = std::max<int64_t>(1, p->num_sms / gy);
+        gx = std::min<int64_t>(gx, a.nchunks);
+        if ((size_t)(gx * I * K) > p->partial_elems) return rtr_set_error(RTR_ENOMEM, "sketch partials exceed workspace");
+        if ((size_t)(gx * gy) > p->normx_part_elems) return rtr_set_error(RTR_ENOMEM, "norm partials exceed workspace");
+        a.partial = p->partial;
+        a.normp = norm_done ? nullptr : p->normx_part;
+        RTR_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sketch_tc_kernel<<<dim3((unsigned)gx, (unsigned)gy), NTHREADS, smem, s>>>(a);
+        RTR_LAUNCH_CHECK("sketch_tc_kernel");
+        const int64_t count = I * K;
+        tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
+            p->partial, (int)gx, count, Y[n], p->normx_part, (int)(gx * gy), norm_done ? nullptr : p->scal + 0);
+        RTR_LAUNCH_CHECK("tc_reduce_kernel");
+        norm_done = true;
+    }
+    if (!norm_done) return launch_sumsq(X, 0, p->numel, p->partial, 1024, p->scal + 0, s);
+    return RTR_OK;
 }
+
+// ---- tensor-core mode product of the last mode ------------------------------
+// Algorithm 1 step 7 for the mode with B = 1 (X viewed as rows a of length I):
+//     T[a, k] = sum_i X[a, i] Q[i, k]
+// D += Xhi Qhi + Xlo Qhi + Xhi Qlo on tcgen05 (BF16 inputs, FP32 accumulation);
+// Q (float64) is split once into resident bf16 hi/lo tiles.  Work unit = one
+// 128-row tile of X and one 64-wide chunk of i.  Warps: 8 converters (loads
+// prefetched one unit ahead), 1 MMA issuer, 4 epilogue warps draining a
+// double-buffered TMEM accumulator into T.
+namespace {
+
+constexpr int TT_CONV_WARPS = 8;
+constexpr int TT_MMA_WARP = TT_CONV_WARPS;
+constexpr int TT_EPI_WARP0 = TT_CONV_WARPS + 1;
+constexpr int TT_NTHREADS = (TT_CONV_WARPS + 1 + 4) * 32;
+constexpr int TT_CONV_THREADS = TT_CONV_WARPS * 32;
+constexpr int TT_PIECES = 128 * 16 / TT_CONV_THREADS;    // float4 pieces per converter thread per unit
+
+struct TtmTCArgs {
+    const float* X;
+    const double* Q;
+    float* out;
+    int64_t A;
+    int I, K, N, NKC, S, vec;
+    int64_t ntiles;
+    int* flags;
+};
+
+__global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    uint8_t* sm = smem_raw + pad;
+    const uint32_t btile = (uint32_t)p.N * 128u;
+    const uint32_t b_bytes = 2u * p.NKC * btile;               // Q hi tiles, then Q lo tiles
+    const uint32_t a_stage = 2u * MTILE_BYTES;                 // X hi, X lo
+    const int S = p.S;
+    const uint32_t bbase = smem_u32(sm);
+    const uint32_t abase = bbase + b_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + b_bytes + S * a_stage);
+    uint64_t* fullA = bars;
+    uint64_t* empty = bars + S;
+    uint64_t* accf = bars + 2 * S;      // [2]
+    uint64_t* acce = bars + 2 * S + 2;  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ncols = 2u * p.N;
+
+    // ---- set-up: zero A stages, build Q hi/lo tiles, barriers, TMEM
+    for (uint32_t off = tid * 16u; off < (uint32_t)S * a_stage; off += TT_NTHREADS * 16u)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(abase + off), "r"(0) : "memory");
+    for (int e = tid; e < p.NKC * p.N * 32; e += TT_NTHREADS) {
+        const int c = e / (p.N * 32), rem = e % (p.N * 32);
+        const int k = rem / 32, ip = rem % 32;          // bf16 pair (2 ip, 2 ip + 1) of chunk c, row k
+        const int i0 = c * 64 + 2 * ip;
+        const float q0 = (k < p.K && i0 < p.I) ? (float)p.Q[(int64_t)i0 * p.K + k] : 0.f;
+        const float q1 = (k < p.K && i0 + 1 < p.I) ? (float)p.Q[(int64_t)(i0 + 1) * p.K + k] : 0.f;
+        uint32_t h, l;
+        split2(q0, q1, h, l);
+        const uint32_t off = sw128_off(k, 2 * ip);
+        st_shared_u32(bbase + c * btile + off, h);
+        st_shared_u32(bbase + (p.NKC + c) * btile + off, l);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&fullA[s], TT_CONV_THREADS);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 128);
+        }
+        *abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == TT_MMA_WARP) tmem_alloc(tmem_slot, ncols);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t nloc = (blockIdx.x < p.ntiles) ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nunits = nloc * p.NKC;
+
+    if (warp < TT_CONV_WARPS) {
+        // ================================================================ converters
+        const int ct = tid;
+        auto load = [&](int64_t u, float4 (&v)[TT_PIECES]) {
+            const int64_t j = u / p.NKC;
+            const int c = (int)(u % p.NKC);
+            const int64_t a0 = (blockIdx.x + j * gridDim.x) * 128;
+            const int rows = (int)min((int64_t)128, p.A - a0);
+#pragma unroll
+            for (int q = 0; q < TT_PIECES; ++q) {
+                const int pc = ct + TT_CONV_THREADS * q;
+                const int row = pc >> 4, c4 = pc & 15;
+                const int i = c * 64 + 4 * c4;
+                v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row < rows && i < p.I) {
+                    const float* src = p.X + (a0 + row) * (int64_t)p.I + i;
+                    if (p.vec) v[q] = __ldg(reinterpret_cast<const float4*>(src));
+                    else {
+                        v[q].x = src[0];
+                        if (i + 1 < p.I) v[q].y = src[1];
+                        if (i + 2 < p.I) v[q].z = src[2];
+                        if (i + 3 < p.I) v[q].w = src[3];
+                    }
+                }
+            }
+        };
+        auto store = [&](int64_t u, const float4 (&v)[TT_PIECES]) {
+            const int s = (int)(u % S);
+            const uint32_t hi = abase + s * a_stage, lo = hi + MTILE_BYTES;
+#pragma unroll
+            for (int q = 0; q < TT_PIECES; ++q) {
+                const int pc = ct + TT_CONV_THREADS * q;
+                const int row = pc >> 4, c4 = pc & 15;
+                uint32_t h0, l0, h1, l1;
+                split2(v[q].x, v[q].y, h0, l0);
+                split2(v[q].z, v[q].w, h1, l1);
+                const uint32_t off = sw128_off(row, 4 * c4);
+                st_shared_v2(hi + off, h0, h1);
+                st_shared_v2(lo + off, l0, l1);
+            }
+        };
+        float4 va[TT_PIECES], vb[TT_PIECES];
+        if (nunits > 0) load(0, va);
+        for (int64_t u = 0; u < nunits; u += 2) {
+            // unit u in va (loaded earlier); prefetch u + 1 into vb
+            if (u + 1 < nunits) load(u + 1, vb);
+            {
+                const int s = (int)(u % S);
+                const uint32_t ph = (uint32_t)(u / S);
+                if (u >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
+                store(u, va);
+                fence_proxy_async();
+                mbar_arrive(&fullA[s]);
+            }
+            if (u + 1 >= nunits) break;
+            if (u + 2 < nunits) load(u + 2, va);
+            {
+                const int64_t u1 = u + 1;
+                const int s = (int)(u1 % S);
+                const uint32_t ph = (uint32_t)(u1 / S);
+                if (u1 >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
+                store(u1, vb);
+                fence_proxy_async();
+                mbar_arrive(&fullA[s]);
+            }
+        }
+    } else if (warp == TT_MMA_WARP) {
+        // ================================================================ MMA issuer
+        const uint32_t idesc = idesc_bf16_f32(128, p.N);
+        bool ok = true;
+        for (int64_t j = 0; j < nloc && ok; ++j) {
+            const int buf = (int)(j & 1);
+            if (j >= 2 && !mbar_wait(&acce[buf], (uint32_t)(((j >> 1) - 1) & 1), abort, p.flags)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(buf * p.N);
+            for (int c = 0; c < p.NKC; ++c) {
+                const int64_t u = j * p.NKC + c;
+                const int s = (int)(u % S);
+                if (!mbar_wait(&fullA[s], (uint32_t)((u / S) & 1), abort, p.flags)) { ok = false; break; }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t ahi = abase + s * a_stage, alo = ahi + MTILE_BYTES;
+                    const uint32_t bhi = bbase + c * btile, blo = bbase + (p.NKC + c) * btile;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t dah = sdesc_sw128(ahi + 32u * kk), dal = sdesc_sw128(alo + 32u * kk);
+                        const uint64_t dbh = sdesc_sw128(bhi + 32u * kk), dbl = sdesc_sw128(blo + 32u * kk);
+                        mma_bf16(d, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(d, dal, dbh, idesc, 1u);
+                        mma_bf16(d, dah, dbl, idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                __syncwarp();
+            }
+            if (ok && lane == 0) mma_commit(&accf[buf]);
+            __syncwarp();
+        }
+    } else {
+        // ================================================================ epilogue
+        const int g = warp & 3;                       // TMEM lane group of this warp
+        for (int64_t j = 0; j < nloc; ++j) {
+            const int buf = (int)(j & 1);
+            if (!mbar_wait(&accf[buf], (uint32_t)((j >> 1) & 1), abort, p.flags)) break;
+            tc_fence_after();
+            const int64_t a0 = (blockIdx.x + j * gridDim.x) * 128;
+            const int64_t row = a0 + 32 * g + lane;
+            for (int c0 = 0; c0 < p.N; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(buf * p.N + c0), v);
+                if (row < p.A) {
+                    float* dst = p.out + row * p.K;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k)
+                        if (c0 + k < p.K) dst[c0 + k] = v[k];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == TT_MMA_WARP) tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace
 
 int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
                   cudaStream_t s) {
-    (void)p; (void)X; (void)A; (void)I; (void)B; (void)Q; (void)K; (void)out; (void)s;
-    return rtr_set_error(RTR_EUNSUPPORTED, "BF16 tensor-core mode product is not built yet");
+    if (B != 1 || I > 256 || K > 64) {
+        // other mode products of BF16 plans run on the SIMT FP32 kernel
+        return launch_ttm(p, 0, X, A, I, B, Q, K, out, s);
+    }
+    TtmTCArgs a{};
+    a.X = X; a.Q = Q; a.out = out; a.A = A; a.I = (int)I; a.K = K;
+    a.N = (K <= 32) ? 32 : 64;
+    a.NKC = (int)rtr_ceil_div(I, 64);
+    a.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && I % 4 == 0) ? 1 : 0;
+    a.ntiles = rtr_ceil_div(A, 128);
+    a.flags = p->flags;
+    const size_t bq = 2 * (size_t)a.NKC * a.N * 128;
+    const size_t fixed = 1024 + 256;
+    int S = (int)((SMEM_LIMIT - fixed - bq) / (2 * MTILE_BYTES));
+    S = std::min(S, 6);
+    if (S < 2) return launch_ttm(p, 0, X, A, I, B, Q, K, out, s);
+    a.S = S;
+    const size_t smem = fixed + bq + (size_t)S * 2 * MTILE_BYTES;
+    const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(a.ntiles, p->num_sms));
+    RTR_CUDA(cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ttm_tc_kernel<<<(unsigned)gx, TT_NTHREADS, smem, s>>>(a);
+    RTR_LAUNCH_CHECK("ttm_tc_kernel");
+    return RTR_OK;
 }

@@ -101,6 +101,8 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->chain[0]); cudaFree(p->chain[1]);
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
     cudaFree(p->flags); cudaFree(p->tc_ws);
+    for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
+    if (p->side) cudaStreamDestroy(p->side);
     delete p;
 }
 
@@ -265,13 +267,22 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     p->als_wmax = 0;
     for (int n = 0; n < N; ++n)
         p->als_wmax = std::max<size_t>(p->als_wmax, (size_t)p->K[n] * R[n] * R[(n + 1) % N]);
-    p->als_ws_elems = (size_t)(RTR_MAXN + 2) * 256 * 256 + 2 * p->als_wmax + 2 * 144 * 144;
+    int64_t maxK = 1, core_elems = 0;
+    for (int n = 0; n < N; ++n) {
+        maxK = std::max<int64_t>(maxK, p->K[n]);
+        core_elems += (((int64_t)R[n] * p->K[n] * R[(n + 1) % N]) + 3) & ~(int64_t)3;
+    }
+    p->als_maxK = (size_t)maxK;
+    p->als_ws_elems = (size_t)(RTR_MAXN + 2) * 256 * 256 + 2 * p->als_wmax + 2 * 144 * 144 + (size_t)maxK +
+                      (size_t)(core_elems / 2 + 8);   // float32 core shadows
     RTR_TRY(dalloc(&p->als_ws, p->als_ws_elems));
     {
         char* sb = nullptr;
         RTR_TRY(dalloc(&sb, 2 * sub_bytes));
         p->sub_ws[0] = sb; p->sub_ws[1] = sb + sub_bytes; p->sub_bytes = sub_bytes;
     }
+    RTR_TRYC(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    for (int e = 0; e < 4; ++e) RTR_TRYC(cudaEventCreateWithFlags(&p->ev[e], cudaEventDisableTiming));
     RTR_TRY(dalloc(&p->flags, 4));
     RTR_TRYC(cudaMemset(p->flags, 0, 4 * sizeof(int)));
     p->tc_ws_bytes = tc_ws_bytes(p);

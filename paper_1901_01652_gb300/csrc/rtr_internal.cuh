@@ -37,6 +37,9 @@ struct rtr_plan {
     double* qr_ws = nullptr;     size_t qr_ws_elems = 0;      // orth workspace
     double* als_ws = nullptr;    size_t als_ws_elems = 0;     // FP64 ALS workspace
     size_t als_wmax = 0;         // max K_n R_n R_{n+1}
+    size_t als_maxK = 0;         // max K_n
+    cudaStream_t side = nullptr; // second stream for work that overlaps the caller's stream
+    cudaEvent_t ev[4] = {};
     void* sub_ws[2] = {nullptr, nullptr}; size_t sub_bytes = 0;  // subchain ping-pong
     int* flags = nullptr;
     void* tc_ws = nullptr;       size_t tc_ws_bytes = 0;       // tensor-core path workspace

@@ -1,0 +1,100 @@
+"""GPU parity of the BF16 (tcgen05, hi+lo split) path against the FP64 oracle.
+
+X is float32 on both sides; Omega is the bfloat16-rounded table on both
+sides.  The only differences are the hi+lo representation of X (relative
+error <= 2^-16 per element) and FP32 accumulation, so the sketch matches the
+oracle to ~1e-5 and the end-to-end reconstruction to the 1e-3 gate."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import rtrd as orc
+from oracle import tensor as ot
+from paper_1901_01652_gb300 import rtr, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1901_01652_gb300 import build
+    build.build()
+    rtr.lib()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+TC_CASES = [
+    ((40, 48, 44, 52), (10, 10, 10, 10)),     # vector paths; last mode transposed (I % 4 == 0)
+    ((257, 19, 6), (64, 7, 5)),              # I > 256: two row groups; K = 64; B % 4 != 0 (scalar)
+    ((9, 130, 7, 33), (5, 40, 3, 20)),       # ragged chunks (B < 64), I = 130 (two M tiles, one partial)
+    ((6, 5, 301), (3, 4, 21)),               # last mode with I % 4 != 0 (scalar transpose path)
+    ((3, 128, 512), (2, 32, 31)),            # B % 64 == 0 vector path, exactly one M tile
+]
+
+
+@pytest.mark.parametrize("dims,K", TC_CASES)
+def test_bf16_sketch_vs_oracle(dims, K):
+    X32 = np.random.default_rng(21).standard_normal(dims).astype(np.float32)
+    plan = rtr.rtr_plan_create(dims, K, (2,) * len(dims),
+                               rtr.make_params("bf16", 77, 3, 1e-2, orc.default_chain_order(dims, K)))
+    Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") if pr else None
+         for d, k, pr in zip(plan.dims, plan.K, plan.projected)]
+    rtr.rtr_sketch(plan, torch.from_numpy(X32).cuda(), Y)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    ref = orc.sketch(X32.astype(np.float64), K, 77, "bf16")
+    for n in range(len(dims)):
+        if ref[n] is not None:
+            assert rel(Y[n].cpu().numpy(), ref[n]) < 2e-5, n
+
+
+def test_bf16_sketch_records_norm():
+    dims, K = (40, 48, 44, 52), (10, 10, 10, 10)
+    X32 = np.random.default_rng(22).standard_normal(dims).astype(np.float32)
+    from paper_1901_01652_gb300.api import RTRD
+    eng = RTRD(dims, K, (2,) * 4, "bf16", 5, 2)
+    Xd = torch.from_numpy(X32).cuda()
+    eng.sketch(Xd)
+    eng.project(Xd)
+    eng.als()
+    eng.compute_rse()
+    torch.cuda.synchronize()
+    # rse^2 = (||X||^2 - ||P||^2 + e^2)/||X||^2 must be a valid fraction
+    r = float(eng.rse.cpu()[0])
+    assert 0.0 < r <= 1.0
+
+
+def test_bf16_end_to_end_vs_oracle():
+    dims, K, R = (48, 40, 44, 52), (10, 10, 10, 10), (3, 3, 3, 3)
+    S = ot.tr_full(workloads.tr_cores(dims, R, 31))
+    X32 = (S + workloads.snr_sigma(ot.fro(S), S.size, 30.0) * workloads.unit_noise(dims, 31)).astype(np.float32)
+    init = workloads.als_init(K, R, 32)
+    ref = orc.rtrd(X32.astype(np.float64), K, R, "als", seed=33, prec="bf16", sweeps=10, init=init)
+    from paper_1901_01652_gb300.api import RTRD
+    eng = RTRD(dims, K, R, "bf16", 33, 10, chain_order=orc.default_chain_order(dims, K))
+    eng.run(torch.from_numpy(X32).cuda(), "als", init=[torch.from_numpy(z) for z in init])
+    Xh = eng.reconstruct("fp64").cpu().numpy()
+    assert rel(Xh, ot.tr_full(ref["G"])) <= 1e-3
+
+
+@pytest.mark.parametrize("dims,K", [((40, 48, 44, 52), (10, 10, 10, 10)),   # last mode first, vector loads
+                                    ((7, 9, 11, 203), (3, 4, 5, 60)),        # I = 203 (scalar path), N = 64
+                                    ((30, 17, 256), (5, 6, 25))])            # I = 256: four full chunks
+def test_bf16_chain_vs_oracle(dims, K):
+    """rtr_project on a BF16 plan (tensor-core first product) from the oracle's Y."""
+    X32 = np.random.default_rng(23).standard_normal(dims).astype(np.float32)
+    X = X32.astype(np.float64)
+    order = orc.default_chain_order(dims, K)
+    plan = rtr.rtr_plan_create(dims, K, (2,) * len(dims), rtr.make_params("bf16", 3, 2, 1e-2, order))
+    Yr = orc.sketch(X, K, 3, "bf16")
+    Yd = [None if y is None else torch.from_numpy(y).cuda() for y in Yr]
+    Q = [torch.zeros((d, k), dtype=torch.float64, device="cuda") for d, k in zip(plan.dims, plan.K)]
+    P = torch.zeros(plan.K, dtype=torch.float32, device="cuda")
+    rtr.rtr_project(plan, torch.from_numpy(X32).cuda(), Yd, Q, P)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    Pr = orc.project(X, [orc.orth(y) for y in Yr], order)
+    assert rel(P.cpu().numpy(), Pr) < 3e-5
