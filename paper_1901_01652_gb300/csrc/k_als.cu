@@ -302,39 +302,40 @@ constexpr int SOLVE_MAXC = 160;       // R_n R_{n+1} <= 144
 // Fast path of the core update: one CTA per slice i of mode n solves
 // G z_i = w_i by mixed-precision iterative refinement (Wilkinson; Moler
 // 1967).  G (float64, already in (beta, alpha) order) is equilibrated,
-// D G D with D = diag(G)^-1/2 in float32, factored by Cholesky in float32 and
-// L^-1 is formed explicitly (one warp per column); each refinement step forms
-// the residual w - G z in float64 and adds D L^-T L^-1 D r (two parallel
-// triangular products), until ||dz|| <= sqrt(tol2) ||z|| or the corrections
-// stop shrinking (the float64 rounding floor).  1024 threads: the factorisation
-// is a chain of C barrier-separated steps whose latency needs many warps.
-// If a float32 pivot is not positive the CTA raises *need_slow and the
-// float64 slow path takes over.  Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
+// D G D with D = diag(G)^-1/2 in float32, and factored by Cholesky in float32
+// (1024 threads: the factorisation is a chain of C barrier-separated steps
+// whose latency needs many warps).  Each refinement step forms the residual
+// w - G z in float64 from the packed Gram matrix in shared memory and adds
+// D (L L^T)^-1 D r (one warp, triangular solves), until ||dz|| <= sqrt(tol2)
+// ||z||, the corrections stop shrinking (the float64 rounding floor), or
+// max_it steps.  If a float32 pivot is not positive the CTA raises
+// *need_slow and the float64 slow path takes over.
+// Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
 constexpr int SOLVE_THREADS = 1024;
 
 __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_fast_kernel(
     const double* __restrict__ G, int Rn, int Rn1, int In, const double* __restrict__ W,
     double* __restrict__ Zn, float* __restrict__ Znf, double* __restrict__ zw_out, int* __restrict__ need_slow,
-    int* __restrict__ flags, double tol2) {
+    int* __restrict__ flags, double tol2, int max_it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int C = Rn * Rn1;
     const int ld = C + 1;
-    const size_t msz = ((size_t)C * ld + 3) & ~(size_t)3;    // keeps every region 16-byte aligned
-    float* Ls = reinterpret_cast<float*>(smem_raw);           // C x ld: Cholesky factor
-    float* Li = Ls + msz;                                     // C x ld: L^-1 (lower)
-    double* z = reinterpret_cast<double*>(Li + msz);
+    const size_t msz = ((size_t)C * ld + 3) & ~(size_t)3;
+    float* Ls = reinterpret_cast<float*>(smem_raw);                  // C x ld: Cholesky factor
+    double* Gp = reinterpret_cast<double*>(Ls + msz);                // packed upper Gram (float64)
+    double* z = Gp + (((size_t)C * (C + 1) / 2 + 1) & ~(size_t)1);
     double* w = z + C;
     double* r = w + C;
     float* sc = reinterpret_cast<float*>(r + C);
-    float* rs = sc + C;
-    float* ys = rs + C;
+    float* invd = sc + C;
+    int* base = reinterpret_cast<int*>(invd + C);
     __shared__ double red[32];
     __shared__ int conv;
     const int i = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tid & 15, ty = tid >> 4, nty = blockDim.x >> 4;
 #ifdef RTR_DEBUG_ITERS
-    long long t_0 = clock64(), t_1 = 0, t_2 = 0, t_3 = 0;
+    long long t_0 = clock64(), t_1 = 0, t_2 = 0;
 #endif
     (void)flags;
 
@@ -343,6 +344,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_fast_kernel(
         sc[c] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 0.f;
         w[c] = W[(int64_t)i * C + c];
         z[c] = 0.0;
+        base[c] = c * C - c * (c - 1) / 2;
     }
     __syncthreads();
     int ok = 1;
@@ -350,9 +352,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_fast_kernel(
     for (int c = ty; c < C; c += nty) {
         const double* grow = G + (int64_t)c * C;
         for (int c2 = tx; c2 < C; c2 += 16) {
-            const float gs = (float)grow[c2] * sc[c] * sc[c2];
+            const double g = grow[c2];
+            const float gs = (float)g * sc[c] * sc[c2];
             if (!isfinite(gs)) ok = 0;
             Ls[c * ld + c2] = gs;
+            if (c2 >= c) Gp[base[c] + c2 - c] = g;
         }
     }
     ok = __syncthreads_and(ok);
@@ -367,95 +371,89 @@ __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_fast_kernel(
         if (tid == 0) atomicExch(need_slow, 1);
         return;
     }
-    // L^-1, column j by warp j mod nwarp: forward substitution of e_j, vector over lanes
-    for (int j = warp; j < C; j += nwarp) {
-        float y[SOLVE_MAXC / 32];
-#pragma unroll
-        for (int t = 0; t < SOLVE_MAXC / 32; ++t) y[t] = (lane + 32 * t == j) ? 1.f : 0.f;
-#pragma unroll
-        for (int ks = 0; ks < SOLVE_MAXC / 32; ++ks) {
-            for (int kk = 0; kk < 32; ++kk) {
-                const int k = ks * 32 + kk;
-                if (k >= C) break;
-                if (k < j) continue;
-                const float yk = __shfl_sync(0xffffffffu, y[ks], kk) / Ls[k * ld + k];
-                if (lane == kk) y[ks] = yk;
-#pragma unroll
-                for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
-                    const int m = lane + 32 * t;
-                    if (m > k && m < C) y[t] -= Ls[m * ld + k] * yk;
-                }
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
-            const int m = lane + 32 * t;
-            if (m < C) Li[m * ld + j] = (m >= j) ? y[t] : 0.f;
-        }
-    }
+    for (int c = tid; c < C; c += blockDim.x) invd[c] = 1.0f / Ls[c * ld + c];
     __syncthreads();
-#ifdef RTR_DEBUG_ITERS
-    t_3 = clock64();
-#endif
     double dz2_prev = 0.0;
     int used = 0;
-    for (int it = 0; it < 12; ++it) {
+    for (int it = 0; it < max_it; ++it) {
         used = it + 1;
-        // r = w - G z in float64: four lanes per row (adjacent), rows in L2-cached G
-        for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
-            const int e = e0 + lane;
-            const int c2 = e >> 2, q = e & 3;
-            double acc = 0.0;
-            if (c2 < C) {
-                const double* grow = G + (int64_t)c2 * C;
-                for (int c = q; c < C; c += 4) acc += z[c] * grow[c];
+        // r = G z in float64 (four adjacent lanes per row, packed upper storage)
+        if (it > 0) {
+            for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
+                const int e = e0 + lane;
+                const int c2 = e >> 2, q = e & 3;
+                double acc = 0.0;
+                if (c2 < C) {
+                    for (int c = q; c < c2; c += 4) acc += z[c] * Gp[base[c] + c2 - c];
+                    const double* row = Gp + base[c2] - c2;
+                    for (int c = c2 + ((q - c2) & 3); c < C; c += 4) acc += z[c] * row[c];
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (c2 < C && q == 0) r[c2] = acc;
             }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (c2 < C && q == 0) rs[c2] = (float)(w[c2] - acc) * sc[c2];
+            __syncthreads();
         }
-        __syncthreads();
-        // ys = L^-1 rs  (row c over lanes of a quad)
-        for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
-            const int e = e0 + lane;
-            const int c = e >> 2, q = e & 3;
-            float acc = 0.f;
-            if (c < C)
-                for (int b = q; b <= c; b += 4) acc = fmaf(Li[c * ld + b], rs[b], acc);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (c < C && q == 0) ys[c] = acc;
-        }
-        __syncthreads();
-        // dz = D L^-T ys
-        double dz2 = 0.0, z2 = 0.0;
-        for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
-            const int e = e0 + lane;
-            const int c = e >> 2, q = e & 3;
-            float acc = 0.f;
-            if (c < C)
-                for (int b = c + q; b < C; b += 4) acc = fmaf(Li[b * ld + c], ys[b], acc);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (c < C && q == 0) {
-                const double dz = (double)(acc * sc[c]);
-                const double zn = z[c] + dz;
-                z[c] = zn;
-                dz2 += dz * dz;
-                z2 += zn * zn;
+        if (warp == 0) {
+            // (L L^T) y = D (w - G z) in float32: one warp, the vector spread over lanes
+            float y[SOLVE_MAXC / 32];
+#pragma unroll
+            for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
+                const int j = lane + 32 * t;
+                y[t] = (j < C) ? (float)(it > 0 ? w[j] - r[j] : w[j]) * sc[j] : 0.f;
             }
+#pragma unroll
+            for (int ks = 0; ks < SOLVE_MAXC / 32; ++ks) {
+                for (int kk = 0; kk < 32; ++kk) {
+                    const int k = ks * 32 + kk;
+                    if (k >= C) break;
+                    const float yk = __shfl_sync(0xffffffffu, y[ks], kk) * invd[k];
+                    if (lane == kk) y[ks] = yk;
+#pragma unroll
+                    for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
+                        const int j = lane + 32 * t;
+                        if (j > k && j < C) y[t] -= Ls[j * ld + k] * yk;
+                    }
+                }
+            }
+#pragma unroll
+            for (int ks = SOLVE_MAXC / 32 - 1; ks >= 0; --ks) {
+                for (int kk = 31; kk >= 0; --kk) {
+                    const int k = ks * 32 + kk;
+                    if (k >= C) continue;
+                    const float xk = __shfl_sync(0xffffffffu, y[ks], kk) * invd[k];
+                    if (lane == kk) y[ks] = xk;
+#pragma unroll
+                    for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
+                        const int j = lane + 32 * t;
+                        if (j < k) y[t] -= Ls[k * ld + j] * xk;
+                    }
+                }
+            }
+            double dz2 = 0.0, z2 = 0.0;
+#pragma unroll
+            for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
+                const int j = lane + 32 * t;
+                if (j < C) {
+                    const double dz = (double)(y[t] * sc[j]);
+                    const double zn = z[j] + dz;
+                    z[j] = zn;
+                    dz2 += dz * dz;
+                    z2 += zn * zn;
+                }
+            }
+            dz2 = rtr::warp_sum(dz2);
+            z2 = rtr::warp_sum(z2);
+            if (lane == 0) conv = (dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25 * dz2_prev)) ? 1 : 0;
+            dz2_prev = dz2;
         }
-        dz2 = rtr::block_sum(dz2, red);
-        z2 = rtr::block_sum(z2, red);
-        if (tid == 0) conv = (dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25 * dz2_prev)) ? 1 : 0;
-        dz2_prev = dz2;
         __syncthreads();
         if (conv) break;
     }
 #ifdef RTR_DEBUG_ITERS
     if (tid == 0 && blockIdx.x == 0)
-        printf("refine iters %d C=%d build %lld chol %lld linv %lld iters %lld clk\n", used, C, t_1 - t_0,
-               t_2 - t_1, t_3 - t_2, clock64() - t_3);
+        printf("refine iters %d C=%d build %lld chol %lld iters %lld clk\n", used, C, t_1 - t_0, t_2 - t_1,
+               clock64() - t_2);
 #else
     (void)used;
 #endif
@@ -868,14 +866,18 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             // ---- join, then solve G z_i = w_i for every slice
             RTR_CUDA(cudaStreamWaitEvent(s, p->ev[1], 0));
             double* G = Mp[0];
-            const size_t fsmem = 2 * sizeof(float) * ((((size_t)C * (C + 1)) + 3) & ~(size_t)3) +
+            const size_t fsmem = sizeof(float) * ((((size_t)C * (C + 1)) + 3) & ~(size_t)3) +
+                                 sizeof(double) * ((((size_t)C * (C + 1) / 2) + 1) & ~(size_t)1) +
                                  3 * sizeof(double) * C + 3 * sizeof(float) * C;
             RTR_CUDA(cudaFuncSetAttribute(als_solve_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)fsmem));
-            // refinement target: float64 accuracy for FP64 plans, 1e-9 relative otherwise
+            // refinement: float64 accuracy for FP64 plans; for the float32 / BF16
+            // plans one float64-residual correction after the float32 solve
+            // (relative error ~(kappa 2^-24)^2)
             const double tol2 = is_f64 ? 1e-28 : 1e-18;
+            const int max_it = is_f64 ? 12 : 2;
             als_solve_fast_kernel<<<(unsigned)I, SOLVE_THREADS, fsmem, s>>>(G, Rn, Rn1, (int)I, W, Z[n], Zf[n], zw,
-                                                                           need_slow, p->flags, tol2);
+                                                                           need_slow, p->flags, tol2, max_it);
             RTR_LAUNCH_CHECK("als_solve_fast_kernel");
             const size_t ssmem = sizeof(double) * (size_t)C * (C + 1);
             RTR_CUDA(cudaFuncSetAttribute(als_solve_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
