@@ -16,6 +16,9 @@
 // every wait is bounded (tc_common.cuh) and raises RTR_FLAG_TIMEOUT.
 // The accumulators D (one 128 x N block per 128-row M tile) live in TMEM.
 #include <algorithm>
+#include <type_traits>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include "rtr_internal.cuh"
 #include "tc_common.cuh"
 
@@ -335,6 +338,286 @@ __global__ void tc_reduce_kernel(const double* __restrict__ partial, int nparts,
     }
 }
 
+// ---- TMA-fed variant for modes with B > 1 ------------------------------------
+// Same arithmetic as sketch_tc_kernel; X tiles (128 rows x 64 values of the
+// (A, I, B) view, rows a*I + i with pitch B) arrive by 2-D TMA into a staging
+// ring, so the loads are always in flight without holding registers.
+//   warps 0-7   converters (staging fp32 -> bf16 hi/lo operand tiles), then
+//               warps 0-3 drain the 128 x N accumulator
+//   warps 8-15  Omega generators, two groups of four taking alternate chunks
+//               (one Philox4x64-10 call per thread per chunk is the longest
+//               dependent chain of the pipeline)
+//   warp 16     TMA producer (one lane)
+//   warp 17     MMA issuer (one lane)
+constexpr int TM_CONV_WARPS = 8;
+constexpr int TM_RNG_GROUPS = 2;
+constexpr int TM_RNG_WARPS = 4 * TM_RNG_GROUPS;
+constexpr int TM_TMA_WARP = TM_CONV_WARPS + TM_RNG_WARPS;
+constexpr int TM_MMA_WARP = TM_TMA_WARP + 1;
+constexpr int TM_NTHREADS = (TM_MMA_WARP + 1) * 32;
+constexpr int TM_CONV_THREADS = TM_CONV_WARPS * 32;
+constexpr int TM_RNG_THREADS = 128;               // threads of one RNG group
+constexpr uint32_t TM_STAGE_X = 128 * 64 * 4;     // fp32 staging tile
+
+struct SketchTmaArgs {
+    int64_t A, B;
+    int I, K, N, S_st, S_op;
+    int kc;                       // chunk width along b: a multiple of 8 dividing B (or 64)
+    int64_t nchunks, nbc;
+    uint64_t seed;
+    int mode;
+    const uint16_t* tab;
+    double* partial;
+    double* normp;
+    int* flags;
+};
+
+__global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                   const SketchTmaArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    uint8_t* sm = smem_raw + pad;
+    const int S_st = p.S_st, S_op = p.S_op;
+    const uint32_t b_bytes = (uint32_t)p.N * 128u;
+    const uint32_t op_bytes = 2 * MTILE_BYTES + b_bytes;
+    const uint32_t st0 = smem_u32(sm);
+    const uint32_t op0 = st0 + S_st * TM_STAGE_X;
+    uint16_t* tab = reinterpret_cast<uint16_t*>(sm + S_st * TM_STAGE_X + S_op * op_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tab + 4096);
+    uint64_t* stfull = bars;
+    uint64_t* stempty = bars + S_st;
+    uint64_t* fullA = bars + 2 * S_st;
+    uint64_t* fullB = fullA + S_op;
+    uint64_t* empty = fullB + S_op;
+    uint64_t* accf = empty + S_op;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    double* nred = reinterpret_cast<double*>(accf + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ncols = (uint32_t)p.N;
+
+    for (uint32_t off = tid * 16u; off < (uint32_t)S_op * op_bytes; off += TM_NTHREADS * 16u)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(op0 + off), "r"(0) : "memory");
+    for (int j = tid; j < 4096; j += TM_NTHREADS) tab[j] = p.tab[j];
+    if (tid == 0) {
+        // one arrival per warp (lane 0 after __syncwarp): same-address
+        // arrivals from every thread serialise on the barrier word
+        for (int s = 0; s < S_st; ++s) {
+            mbar_init(&stfull[s], 1);
+            mbar_init(&stempty[s], TM_CONV_WARPS);
+        }
+        for (int s = 0; s < S_op; ++s) {
+            mbar_init(&fullA[s], TM_CONV_WARPS);
+            mbar_init(&fullB[s], TM_RNG_THREADS / 32);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        *abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == TM_MMA_WARP) tmem_alloc(tmem_slot, ncols < 32 ? 32 : ncols);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int rbeg = blockIdx.y * 128;
+    const int rows_valid = min(128, p.I - rbeg);
+    const int64_t nloc = (blockIdx.x < p.nchunks) ? (p.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    double nsum = 0.0;
+
+    if (warp < TM_CONV_WARPS) {
+        // ================================================================ converters
+        const int ct = tid;
+        for (int64_t t = 0; t < nloc; ++t) {
+            const int ss = (int)(t % S_st), so = (int)(t % S_op);
+            const uint32_t us = (uint32_t)(t / S_st), uo = (uint32_t)(t / S_op);
+            if (!mbar_wait(&stfull[ss], us & 1, abort, p.flags)) break;
+            if (t >= S_op && !mbar_wait(&empty[so], (uo - 1) & 1, abort, p.flags)) break;
+            const uint32_t src = st0 + ss * TM_STAGE_X;
+            const uint32_t hi = op0 + so * op_bytes, lo = hi + MTILE_BYTES;
+            float csum = 0.f;
+            auto piece = [&](const float4 v, int row, int c4) {
+                uint32_t h0, l0, h1, l1;
+                split2(v.x, v.y, h0, l0);
+                split2(v.z, v.w, h1, l1);
+                if (row < rows_valid) csum += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                const uint32_t off = sw128_off(row, 4 * c4);
+                st_shared_v2(hi + off, h0, h1);
+                st_shared_v2(lo + off, l0, l1);
+            };
+            if (p.kc == 64) {
+                // 8 float4 pieces per thread: all loads issued before any conversion
+                float4 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int pc = ct + TM_CONV_THREADS * j;
+                    v[j] = ld_shared_f4(src + (uint32_t)(pc >> 4) * 256u + (uint32_t)(pc & 15) * 16u);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int pc = ct + TM_CONV_THREADS * j;
+                    piece(v[j], pc >> 4, pc & 15);
+                }
+            } else {
+                // kc = 4 Q4 with Q4 a compile-time constant: row/column of a piece
+                // by multiply-shift, loads batched like the full-width case
+                auto run = [&](auto q4c) {
+                    constexpr int Q4 = decltype(q4c)::value;
+                    constexpr int NP = (128 * Q4 + TM_CONV_THREADS - 1) / TM_CONV_THREADS;
+                    float4 v[NP];
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const int pc = ct + TM_CONV_THREADS * j;
+                        if (pc < 128 * Q4)
+                            v[j] = ld_shared_f4(src + (uint32_t)(pc / Q4) * (uint32_t)(16 * Q4) + (uint32_t)(pc % Q4) * 16u);
+                    }
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const int pc = ct + TM_CONV_THREADS * j;
+                        if (pc < 128 * Q4) piece(v[j], pc / Q4, pc % Q4);
+                    }
+                };
+                switch (p.kc >> 2) {
+                    case 2: run(std::integral_constant<int, 2>{}); break;
+                    case 4: run(std::integral_constant<int, 4>{}); break;
+                    case 6: run(std::integral_constant<int, 6>{}); break;
+                    case 8: run(std::integral_constant<int, 8>{}); break;
+                    case 10: run(std::integral_constant<int, 10>{}); break;
+                    case 12: run(std::integral_constant<int, 12>{}); break;
+                    default: run(std::integral_constant<int, 14>{}); break;
+                }
+            }
+            nsum += (double)csum;
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&fullA[so]);
+                mbar_arrive(&stempty[ss]);
+            }
+        }
+    } else if (warp < TM_TMA_WARP) {
+        // ================================================================ Omega generators
+        const int rt = (tid - TM_CONV_THREADS) % TM_RNG_THREADS;
+        const int grp = (tid - TM_CONV_THREADS) / TM_RNG_THREADS;
+        const int ncall = (p.K + 19) / 20;
+        for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS) {
+            const int64_t ch = blockIdx.x + t * gridDim.x;
+            const int so = (int)(t % S_op);
+            const uint32_t uo = (uint32_t)(t / S_op);
+            const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * p.kc;
+            const int64_t r0 = a * p.B + b0;
+            const int len = (int)min((int64_t)p.kc, p.B - b0);
+            if (t >= S_op && !mbar_wait(&empty[so], (uo - 1) & 1, abort, p.flags)) break;
+            const uint32_t bt = op0 + so * op_bytes + 2 * MTILE_BYTES;
+            for (int item = rt; item < p.kc * ncall; item += TM_RNG_THREADS) {
+                const int rr = item % p.kc, cb = item / p.kc;
+                uint64_t w[4] = {0, 0, 0, 0};
+                if (rr < len) rtr::omega_words(p.seed, p.mode, (uint64_t)(r0 + rr), (uint64_t)cb, w);
+#pragma unroll
+                for (int tt = 0; tt < 20; ++tt) {
+                    const int k = cb * 20 + tt;
+                    if (k < p.K) st_shared_u16(bt + sw128_off(k, rr), (rr < len) ? tab[rtr::omega_field(w, tt)] : (uint16_t)0);
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&fullB[so]);
+        }
+    } else if (warp == TM_TMA_WARP) {
+        // ================================================================ TMA producer
+        if (lane == 0) {
+            for (int64_t t = 0; t < nloc; ++t) {
+                const int64_t ch = blockIdx.x + t * gridDim.x;
+                const int ss = (int)(t % S_st);
+                const uint32_t us = (uint32_t)(t / S_st);
+                if (t >= S_st && !mbar_wait(&stempty[ss], (us - 1) & 1, abort, p.flags)) break;
+                const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * p.kc;
+                // the full box is always counted: out-of-range rows (i >= I) and
+                // columns are zero-filled by the TMA unit without memory traffic
+                mbar_arrive_expect_tx(&stfull[ss], (uint32_t)(128 * 4 * p.kc));
+                tma_load_3d(st0 + ss * TM_STAGE_X, &tmap, (int)b0, rbeg, (int)a, &stfull[ss]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ================================================================ MMA issuer
+        const uint32_t idesc = idesc_bf16_f32(128, p.N);
+        for (int64_t t = 0; t < nloc; ++t) {
+            const int so = (int)(t % S_op);
+            const uint32_t uo = (uint32_t)(t / S_op);
+            if (!mbar_wait(&fullA[so], uo & 1, abort, p.flags)) break;
+            if (!mbar_wait(&fullB[so], uo & 1, abort, p.flags)) break;
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t ahi = op0 + so * op_bytes, alo = ahi + MTILE_BYTES, bb = ahi + 2 * MTILE_BYTES;
+                const int ksteps = (p.kc + 15) >> 4;      // columns kc..16*ksteps-1 stay zero
+                for (int j = 0; j < ksteps; ++j) {
+                    const uint64_t bd = sdesc_sw128(bb + 32u * j);
+                    mma_bf16(tmem, sdesc_sw128(ahi + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
+                    mma_bf16(tmem, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
+                }
+                mma_commit(&empty[so]);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) mma_commit(accf);
+        __syncwarp();
+    }
+
+    // ==================================================================== epilogue
+    if (warp < 4) {
+        const bool have = nloc > 0;
+        bool ok = true;
+        if (have) {
+            ok = mbar_wait(accf, 0, abort, p.flags);
+            tc_fence_after();
+        }
+        const int row = 32 * warp + lane;
+        for (int c0 = 0; c0 < p.N; c0 += 32) {
+            float v[32];
+            if (have && ok) {
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = 0.f;
+            }
+            if (row < rows_valid) {
+                double* dst = p.partial + ((int64_t)blockIdx.x * p.I + rbeg + row) * p.K;
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (c0 + k < p.K) dst[c0 + k] = (double)v[k];
+            }
+        }
+    }
+    if (warp < TM_CONV_WARPS && p.normp) {
+        nsum = rtr::warp_sum(nsum);
+        if (lane == 0) nred[warp] = nsum;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (p.normp && tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < TM_CONV_WARPS; ++w) s += nred[w];
+        p.normp[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+    if (warp == TM_MMA_WARP) tmem_dealloc(tmem, ncols < 32 ? 32 : ncols);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
 constexpr size_t SMEM_LIMIT = 232448;   // 227 KiB opt-in per CTA
 
 int sketch_geometry(int64_t I, int K, int* MT, int* N, int* S, size_t* smem) {
@@ -352,6 +635,56 @@ int sketch_geometry(int64_t I, int K, int* MT, int* N, int* S, size_t* smem) {
 
 }  // namespace
 
+int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
+                      double* norm_out, cudaStream_t s) {
+    const int K = p->K[n];
+    SketchTmaArgs a{};
+    a.A = A; a.B = B; a.I = (int)I; a.K = K;
+    a.N = (K <= 32) ? 32 : 64;
+    // chunk width: 64, or the largest multiple of 8 up to 64 that divides B
+    // (no ragged tail chunk, e.g. 40 for B = 200)
+    a.kc = 64;
+    if (B % 64 != 0) {
+        for (int w = 56; w >= 8; w -= 8)
+            if (B % w == 0) { a.kc = w; break; }
+    }
+    a.nbc = rtr_ceil_div(B, a.kc);
+    a.nchunks = A * a.nbc;
+    a.seed = p->params.seed; a.mode = n;
+    a.tab = p->tab_bf16; a.flags = p->flags;
+    const size_t fixed = 8192 + 64 * 8 + 2048;
+    const size_t op = 2 * (size_t)MTILE_BYTES + (size_t)a.N * 128;
+    a.S_st = 3;
+    a.S_op = (int)std::min<size_t>(3, (SMEM_LIMIT - fixed - 3 * (size_t)TM_STAGE_X) / op);
+    if (a.S_op < 2) { a.S_st = 2; a.S_op = (int)std::min<size_t>(3, (SMEM_LIMIT - fixed - 2 * (size_t)TM_STAGE_X) / op); }
+    const size_t smem = fixed + (size_t)a.S_st * TM_STAGE_X + (size_t)a.S_op * op;
+    const int gy = (int)rtr_ceil_div(I, 128);
+    int64_t gx = std::max<int64_t>(1, p->num_sms / gy);
+    gx = std::min<int64_t>(gx, a.nchunks);
+    if ((size_t)(gx * I * K) > p->partial_elems) return rtr_set_error(RTR_ENOMEM, "sketch partials exceed workspace");
+    if ((size_t)(gx * gy) > p->normx_part_elems) return rtr_set_error(RTR_ENOMEM, "norm partials exceed workspace");
+    a.partial = p->partial;
+    a.normp = norm_out ? p->normx_part : nullptr;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[3] = {(cuuint64_t)B, (cuuint64_t)I, (cuuint64_t)A};
+    const cuuint64_t gstride[2] = {(cuuint64_t)B * 4, (cuuint64_t)I * B * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)a.kc, 128, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), gdim,
+                                             gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    RTR_CUDA(cudaFuncSetAttribute(sketch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    sketch_tma_kernel<<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+    RTR_LAUNCH_CHECK("sketch_tma_kernel");
+    const int64_t count = I * K;
+    tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(p->partial, (int)gx, count, Y,
+                                                                          p->normx_part, (int)(gx * gy), norm_out);
+    RTR_LAUNCH_CHECK("tc_reduce_kernel");
+    return RTR_OK;
+}
+
 size_t tc_ws_bytes(const rtr_plan* p) { (void)p; return 0; }
 
 int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s) {
@@ -361,6 +694,13 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
         int64_t A, I, B;
         rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
         const int K = p->K[n];
+        const bool aligned16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+        if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder()) {
+            int st = launch_sketch_tma(p, X, A, I, B, n, Y[n], norm_done ? nullptr : p->scal + 0, s);
+            if (st) return st;
+            norm_done = true;
+            continue;
+        }
         int MT, N, S;
         size_t smem;
         if (!sketch_geometry(I, K, &MT, &N, &S, &smem))

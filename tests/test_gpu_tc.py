@@ -32,6 +32,7 @@ TC_CASES = [
     ((9, 130, 7, 33), (5, 40, 3, 20)),       # ragged chunks (B < 64), I = 130 (two M tiles, one partial)
     ((6, 5, 301), (3, 4, 21)),               # last mode with I % 4 != 0 (scalar transpose path)
     ((3, 128, 512), (2, 32, 31)),            # B % 64 == 0 vector path, exactly one M tile
+    ((5, 300, 36), (3, 40, 7)),              # TMA path: I = 300 (three row groups), B = 36 < 64 (ragged)
 ]
 
 
