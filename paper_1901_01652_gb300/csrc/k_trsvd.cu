@@ -1,7 +1,297 @@
-// TR-SVD on the projected tensor (Algorithm 1 step 9, second decomposer).
+// TR-SVD on the projected tensor (Algorithm 1 step 9, second decomposer;
+// Section 4.1 tolerance), float64.
+//
+// Step k works on the unfolding C_k (rows x cols, row-major float64):
+//   C_0 = P as K_1 x (K_2 ... K_N)
+//   SVD C_k = U S V^T through the Gram matrix of the smaller side (float64,
+//   many CTAs) and its Jacobi eigendecomposition (one CTA, float64);
+//   rank r_k = smallest r with sqrt(sum_{i>=r} s_i^2) <= threshold (sqrt(2)
+//   delta for k = 0, delta after; delta = tol ||P|| / sqrt(N)), or forced;
+//   core k = U_r reshaped, carry = S_r V_r^T = U_r^T C_k, which is reshaped
+//   (and, after the first step, cyclically permuted) into C_{k+1}.
+// The last core is the final carry.  Each rank decision is read back to the
+// host (the next shapes depend on it).
+#include <algorithm>
+#include <cmath>
+#include <vector>
 #include "rtr_internal.cuh"
+#include "dense.cuh"
+
+namespace {
+
+inline unsigned gridn(int64_t n, int t = 256) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
+}
+
+// G = C C^T (left) or C^T C (right), m x m float64, one output per thread.
+template <typename T>
+__global__ void gram_kernel(const T* __restrict__ Cm, int64_t rows, int64_t cols, int left, double* __restrict__ G) {
+    const int64_t m = left ? rows : cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / m, j = e % m;
+        if (j < i) continue;
+        double s = 0.0;
+        if (left)
+            for (int64_t l = 0; l < cols; ++l) s += (double)Cm[i * cols + l] * (double)Cm[j * cols + l];
+        else
+            for (int64_t l = 0; l < rows; ++l) s += (double)Cm[l * cols + i] * (double)Cm[l * cols + j];
+        G[i * m + j] = s;
+        G[j * m + i] = s;
+    }
+}
+
+// Jacobi eigendecomposition of G (m x m, global memory) in one CTA; then sort
+// eigenpairs by decreasing eigenvalue into lam[m] and Vs (m x m, columns).
+__global__ void __launch_bounds__(1024) eig_kernel(double* __restrict__ G, double* __restrict__ V, int m,
+                                                   double* __restrict__ lam, double* __restrict__ Vs,
+                                                   int* __restrict__ order) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int np = (m + 1) / 2 + 1;
+    double* cs = reinterpret_cast<double*>(smem_raw);            // 2 np
+    int* pairs = reinterpret_cast<int*>(cs + 2 * np);            // 2 np
+    rtr::block_jacobi_eig(G, V, m, m, pairs, cs, 60);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < m; ++i) order[i] = i;
+        // insertion sort by decreasing eigenvalue (m is small)
+        for (int i = 1; i < m; ++i) {
+            const int o = order[i];
+            const double v = G[(int64_t)o * m + o];
+            int j = i - 1;
+            while (j >= 0 && G[(int64_t)order[j] * m + order[j]] < v) { order[j + 1] = order[j]; --j; }
+            order[j + 1] = o;
+        }
+        for (int i = 0; i < m; ++i) lam[i] = G[(int64_t)order[i] * m + order[i]];
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+        const int64_t r = e / m, c = e % m;
+        Vs[e] = V[r * m + order[c]];
+    }
+}
+
+// rank from the eigenvalue tail: smallest r >= 1 with sum_{i>=r} max(lam_i, 0) <= thr^2
+__global__ void rank_kernel(const double* __restrict__ lam, int m, double thr2, int cap, int* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double tail = 0.0;
+        for (int i = 0; i < m; ++i) tail += fmax(lam[i], 0.0);
+        int r = 0;
+        while (r < m && tail > thr2) { tail -= fmax(lam[r], 0.0); ++r; }
+        r = max(r, 1);
+        out[0] = min(r, cap);
+        out[1] = r > cap;
+    }
+}
+
+// left singular vectors: U[:, :r] for the left Gram: U = Vs[:, :r] (rows x r);
+// for the right Gram: U = C Vs[:, :r] / s   (s = sqrt(lam)).
+template <typename T>
+__global__ void left_vectors_kernel(const T* __restrict__ Cm, int64_t rows, int64_t cols, int left,
+                                    const double* __restrict__ Vs, const double* __restrict__ lam, int m, int r,
+                                    double* __restrict__ U) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * r; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / r, k = e % r;
+        if (left) {
+            U[e] = Vs[i * m + k];
+        } else {
+            double s = 0.0;
+            for (int64_t l = 0; l < cols; ++l) s += (double)Cm[i * cols + l] * Vs[l * m + k];
+            const double sg = sqrt(fmax(lam[k], 0.0));
+            U[e] = sg > 0.0 ? s / sg : 0.0;
+        }
+    }
+}
+
+// carry = U^T C  (r x cols)
+template <typename T>
+__global__ void carry_kernel(const T* __restrict__ Cm, int64_t rows, int64_t cols, const double* __restrict__ U, int r,
+                             double* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)r * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / cols, j = e % cols;
+        double s = 0.0;
+        for (int64_t i = 0; i < rows; ++i) s += U[i * r + k] * (double)Cm[i * cols + j];
+        out[e] = s;
+    }
+}
+
+// core 0: U (K_0 x R0 R1) -> Z (R0, K_0, R1)
+__global__ void core0_kernel(const double* __restrict__ U, int K0, int R0, int R1, double* __restrict__ Z) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K0 * R0 * R1; e += gridDim.x * blockDim.x) {
+        const int b = e % R1, i = (e / R1) % K0, a = e / (R1 * K0);
+        Z[e] = U[(int64_t)i * (R0 * R1) + a * R1 + b];
+    }
+}
+
+// first carry (R0, R1, rest) -> (R1, rest, R0)
+__global__ void permute_first_kernel(const double* __restrict__ in, int R0, int R1, int64_t rest,
+                                     double* __restrict__ out) {
+    const int64_t total = (int64_t)R0 * R1 * rest;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % R0);
+        const int64_t x = (e / R0) % rest;
+        const int b = (int)(e / ((int64_t)R0 * rest));
+        out[e] = in[((int64_t)a * R1 + b) * rest + x];
+    }
+}
+
+__global__ void copy_kernel(const double* __restrict__ in, int64_t n, double* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = in[e];
+}
+
+template <typename T>
+__global__ void sumsq_svd_kernel(const T* __restrict__ X, int64_t n, double* __restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        s += (double)X[e] * (double)X[e];
+    s = rtr::block_sum(s, red);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+struct SvdWs {
+    double *Cbuf0, *Cbuf1, *G, *V, *Vs, *U, *lam;
+    int* iv;           // [0..1] rank, overflow; [2..] order
+    double* nrm;
+};
+
+// one truncated SVD of C (rows x cols); returns rank (host), writes U (rows x r)
+// and the carry (r x cols) into ws
+template <typename T>
+int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, int cap, SvdWs& w, int* r_out,
+             int* overflow, cudaStream_t s) {
+    const int left = rows <= cols;
+    const int m = (int)(left ? rows : cols);
+    gram_kernel<T><<<gridn((int64_t)m * m), 256, 0, s>>>(Cm, rows, cols, left, w.G);
+    RTR_LAUNCH_CHECK("gram_kernel");
+    const size_t np = (size_t)(m + 1) / 2 + 1;
+    const size_t smem = 2 * np * (sizeof(double) + sizeof(int));
+    eig_kernel<<<1, 1024, smem, s>>>(w.G, w.V, m, w.lam, w.Vs, w.iv + 2);
+    RTR_LAUNCH_CHECK("eig_kernel");
+    int r = forced;
+    if (forced <= 0) {
+        rank_kernel<<<1, 32, 0, s>>>(w.lam, m, thr * thr, std::min(cap, m), w.iv);
+        RTR_LAUNCH_CHECK("rank_kernel");
+        int h[2];
+        RTR_CUDA(cudaMemcpyAsync(h, w.iv, sizeof(h), cudaMemcpyDeviceToHost, s));
+        RTR_CUDA(cudaStreamSynchronize(s));
+        r = h[0];
+        *overflow |= h[1];
+    }
+    if (r < 1 || r > m) return rtr_set_error(RTR_EINVAL, "TR-SVD rank %d outside [1, %d]", r, m);
+    left_vectors_kernel<T><<<gridn(rows * r), 256, 0, s>>>(Cm, rows, cols, left, w.Vs, w.lam, m, r, w.U);
+    RTR_LAUNCH_CHECK("left_vectors_kernel");
+    *r_out = r;
+    return RTR_OK;
+}
+
+template <typename T>
+int trsvd_impl(rtr_plan* p, const T* P, double tol, double* const* Z, int* ranks, cudaStream_t s) {
+    const int N = p->N;
+    int64_t K[RTR_MAXN];
+    for (int n = 0; n < N; ++n) K[n] = p->K[n];
+    SvdWs w;
+    w.Cbuf0 = p->svd_ws;
+    w.Cbuf1 = w.Cbuf0 + p->svd_cbuf;
+    w.G = w.Cbuf1 + p->svd_cbuf;
+    w.V = w.G + p->svd_gmax * p->svd_gmax;
+    w.Vs = w.V + p->svd_gmax * p->svd_gmax;
+    w.lam = w.Vs + p->svd_gmax * p->svd_gmax;
+    w.U = w.lam + p->svd_gmax;
+    w.nrm = w.U + p->svd_umax;
+    w.iv = reinterpret_cast<int*>(w.nrm + 2);
+    const bool forced = ranks[0] > 0;
+    // delta = tol ||P|| / sqrt(N)
+    RTR_CUDA(cudaMemsetAsync(w.nrm, 0, sizeof(double), s));
+    sumsq_svd_kernel<T><<<256, 256, 0, s>>>(P, p->pnumel, w.nrm);
+    RTR_LAUNCH_CHECK("sumsq_svd_kernel");
+    double nrm2 = 0.0;
+    RTR_CUDA(cudaMemcpyAsync(&nrm2, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RTR_CUDA(cudaStreamSynchronize(s));
+    const double delta = tol * std::sqrt(nrm2) / std::sqrt((double)N);
+    int overflow = 0;
+    int R[RTR_MAXN + 1];
+    // ---- step 0: C_0 = P (K_0 x rest)
+    int64_t rest = p->pnumel / K[0];
+    int cap0 = p->R[0] * p->R[1];
+    int r = 0;
+    int st = svd_step<T>(P, K[0], rest, std::sqrt(2.0) * delta, forced ? ranks[0] * ranks[1] : 0, cap0, w, &r,
+                         &overflow, s);
+    if (st) return st;
+    int R0, R1;
+    if (forced) { R0 = ranks[0]; R1 = ranks[1]; }
+    else {
+        R0 = 1;
+        for (int d = 1; d * d <= r; ++d) if (r % d == 0) R0 = d;
+        R1 = r / R0;
+        if (R0 > p->R[0] || R1 > p->R[1]) {
+            // the split does not fit the plan's core capacity: cap both factors
+            R0 = std::min(R0, p->R[0]);
+            R1 = std::min(R1, p->R[1]);
+            r = R0 * R1;
+            overflow = 1;
+        }
+    }
+    R[0] = R0; R[1] = R1;
+    core0_kernel<<<gridn((int64_t)K[0] * r), 256, 0, s>>>(w.U, (int)K[0], R0, R1, Z[0]);
+    RTR_LAUNCH_CHECK("core0_kernel");
+    carry_kernel<T><<<gridn((int64_t)r * rest), 256, 0, s>>>(P, K[0], rest, w.U, r, w.Cbuf1);
+    RTR_LAUNCH_CHECK("carry_kernel");
+    permute_first_kernel<<<gridn((int64_t)r * rest), 256, 0, s>>>(w.Cbuf1, R0, R1, rest, w.Cbuf0);
+    RTR_LAUNCH_CHECK("permute_first_kernel");
+    double* Ccur = w.Cbuf0;
+    double* Cnext = w.Cbuf1;
+    // ---- steps 1 .. N-2
+    for (int k = 1; k <= N - 2; ++k) {
+        const int64_t rows = (int64_t)R[k] * K[k];
+        const int64_t cols = (int64_t)r * rest / rows;       // total stays r * rest
+        int rk = 0;
+        const int cap = p->R[k + 1];
+        st = svd_step<double>(Ccur, rows, cols, delta, forced ? ranks[k + 1] : 0, cap, w, &rk, &overflow, s);
+        if (st) return st;
+        R[k + 1] = rk;
+        // core k = U reshaped (R_k, K_k, R_{k+1})
+        copy_kernel<<<gridn(rows * rk), 256, 0, s>>>(w.U, rows * rk, Z[k]);
+        RTR_LAUNCH_CHECK("copy_kernel");
+        carry_kernel<double><<<gridn((int64_t)rk * cols), 256, 0, s>>>(Ccur, rows, cols, w.U, rk, Cnext);
+        RTR_LAUNCH_CHECK("carry_kernel");
+        std::swap(Ccur, Cnext);
+        r = rk;
+        rest = cols;
+    }
+    // ---- last core: carry (R_{N-1} x K_{N-1} R_0)
+    copy_kernel<<<gridn((int64_t)R[N - 1] * K[N - 1] * R0), 256, 0, s>>>(Ccur, (int64_t)R[N - 1] * K[N - 1] * R0,
+                                                                          Z[N - 1]);
+    RTR_LAUNCH_CHECK("copy_kernel");
+    for (int n = 0; n < N; ++n) ranks[n] = R[n];
+    if (overflow)
+        return rtr_set_error(RTR_ENOTCONV, "TR-SVD: a chosen rank exceeded the plan's core capacity and was capped");
+    return RTR_OK;
+}
+
+}  // namespace
+
+size_t trsvd_ws_elems(int64_t pnumel, int64_t* cbuf, int64_t* gmax, int64_t* umax) {
+    // every unfolding C_k has at most |P| entries (each carry has no more rows
+    // than the unfolding it came from), the Gram side is <= sqrt(|C_k|), and
+    // U_r (rows x r) fits in |P| entries
+    *cbuf = std::max<int64_t>(pnumel, 1);
+    int64_t g = 1;
+    while (g * g < *cbuf) ++g;
+    *gmax = g;
+    *umax = *cbuf;
+    return (size_t)(2 * *cbuf + 3 * *gmax * *gmax + *gmax + *umax + 4 + *gmax / 2 + 8);
+}
 
 int run_trsvd(rtr_plan* p, const void* P, double tol, double* const* Z, int* ranks, cudaStream_t s) {
-    (void)p; (void)P; (void)tol; (void)Z; (void)ranks; (void)s;
-    return rtr_set_error(RTR_EUNSUPPORTED, "TR-SVD kernels are not built yet");
+    if (!(tol > 0.0)) return rtr_set_error(RTR_EINVAL, "TR-SVD tolerance must be positive");
+    for (int n = 0; n < p->N; ++n) if (!Z[n]) return rtr_set_error(RTR_EINVAL, "Z[%d] is NULL", n);
+    if (ranks[0] > 0) {
+        for (int n = 0; n < p->N; ++n)
+            if (ranks[n] < 1 || ranks[n] > p->R[n])
+                return rtr_set_error(RTR_EINVAL, "forced rank %d of core %d outside [1, %d]", ranks[n], n, p->R[n]);
+    }
+    if (p->params.prec == RTR_FP64) return trsvd_impl<double>(p, (const double*)P, tol, Z, ranks, s);
+    return trsvd_impl<float>(p, (const float*)P, tol, Z, ranks, s);
 }

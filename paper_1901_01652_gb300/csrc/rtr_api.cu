@@ -16,6 +16,7 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
 int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
                   cudaStream_t s);
 size_t tc_ws_bytes(const rtr_plan* p);
+size_t trsvd_ws_elems(int64_t pnumel, int64_t* cbuf, int64_t* gmax, int64_t* umax);
 
 namespace {
 thread_local char g_err[1024] = "";
@@ -100,7 +101,7 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->partial); cudaFree(p->normx_part); cudaFree(p->scal);
     cudaFree(p->chain[0]); cudaFree(p->chain[1]);
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
-    cudaFree(p->flags); cudaFree(p->tc_ws);
+    cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws);
     for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
     if (p->side) cudaStreamDestroy(p->side);
     delete p;
@@ -285,6 +286,7 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     for (int e = 0; e < 4; ++e) RTR_TRYC(cudaEventCreateWithFlags(&p->ev[e], cudaEventDisableTiming));
     RTR_TRY(dalloc(&p->flags, 4));
     RTR_TRYC(cudaMemset(p->flags, 0, 4 * sizeof(int)));
+    RTR_TRY(dalloc(&p->svd_ws, trsvd_ws_elems(p->pnumel, &p->svd_cbuf, &p->svd_gmax, &p->svd_umax)));
     p->tc_ws_bytes = tc_ws_bytes(p);
     if (p->tc_ws_bytes) {
         char* t = nullptr;

@@ -43,6 +43,7 @@ struct rtr_plan {
     void* sub_ws[2] = {nullptr, nullptr}; size_t sub_bytes = 0;  // subchain ping-pong
     int* flags = nullptr;
     void* tc_ws = nullptr;       size_t tc_ws_bytes = 0;       // tensor-core path workspace
+    double* svd_ws = nullptr;    int64_t svd_cbuf = 0, svd_gmax = 0, svd_umax = 0;  // TR-SVD workspace
 };
 
 // ---- error reporting (rtr_api.cu) -------------------------------------------
