@@ -16,6 +16,9 @@ Application to Large-scale Data Reconstruction", arXiv:1901.01652):
 * ``tensor``  - unfoldings, mode-n products, TR format (Eq. 1, Eq. 2).
 * ``rtrd``    - Algorithm 1 (sketch, QR, projection, back-projection), the
                 TR-ALS and TR-SVD decomposers it calls, RSE (Section 4).
+* ``proposer`` - the learned proposer of K_n and R_n (this build's own
+                definition; the paper fixes them by hand in Section 4):
+                spectrum features, MLP forward/backward, Adam, decoding.
 
 Pins: every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` against closed forms, brute force on tiny inputs,
