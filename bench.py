@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch256"],
+                    help="c2 = the 200^4 tensor (default); batch256 = 256 uneven image-like tensors")
+    ap.add_argument("--streams", type=int, default=16, help="worker streams of the batched form")
     return ap.parse_args()
 
 
@@ -371,9 +374,144 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched form
+
+BATCH_WORKLOAD = ("256 image-like order-4 fp32 tensors, modes U{32..96}, TR rank r ~ U{4..12} (smoothed spatial "
+                  "cores, 0..255 integer pixels), K_n = min(I_n, 2r), R_n = r, 20 sweeps")
+
+
+def batch_inputs(device, count=256):
+    """The batched workload on the device: per tensor t, smoothed TR cores
+    (seed 1905 + 31 t) expanded by the library's reconstruct, mapped to pixels."""
+    import torch
+    from paper_1901_01652_gb300 import rtr, workloads
+    cfg = workloads.CONFIGS["c4_batch256"]
+    shapes = workloads.batch_shapes(count, cfg["lo"], cfg["hi"], cfg["rlo"], cfg["rhi"], cfg["seed"])
+    Xs, Ks, Rs = [], [], []
+    for t, (dims, r) in enumerate(shapes):
+        cores = [torch.from_numpy(c).to(device) for c in workloads.smoothed_tr_cores(dims, r, cfg["seed"] + 31 * t)]
+        X = torch.empty(dims, dtype=torch.float32, device=device)
+        R = [r] * 4
+        work = torch.empty(rtr.rtr_reconstruct_work_bytes(dims, R), dtype=torch.uint8, device=device)
+        rtr.rtr_reconstruct(dims, R, cores, "fp32", X, work)
+        Xs.append(workloads.to_pixels(X))
+        K, Rr = workloads.batch_ranks(dims, r)
+        Ks.append(K)
+        Rs.append(Rr)
+    torch.cuda.synchronize()
+    return [s[0] for s in shapes], Xs, Ks, Rs, cfg
+
+
+def batch_cpu_baseline(shapes, Ks, Rs, cfg, budget_s=15.0):
+    """The FP64 oracle on the first tensors of the batch, one by one, until
+    about budget_s seconds of work; returns GB/s of float32 input."""
+    from oracle import rtrd as orc
+    from oracle import tensor as ot
+    from paper_1901_01652_gb300 import workloads
+    tot_b, tot_s, n = 0, 0.0, 0
+    for t, dims in enumerate(shapes):
+        X = workloads.to_pixels(ot.tr_full(workloads.smoothed_tr_cores(dims, Rs[t][0], cfg["seed"] + 31 * t)))
+        X = X.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        out = orc.rtrd(X, Ks[t], Rs[t], "als", seed=cfg["seed"] + t, prec="bf16", sweeps=cfg["sweeps"])
+        orc.rse_identity(ot.fro(X) ** 2, out["P"], out["Z"])
+        tot_s += time.perf_counter() - t0
+        tot_b += X.size * 4
+        n += 1
+        if tot_s >= budget_s:
+            break
+    return {"value": round(tot_b / tot_s / 1e9, 6), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {n} tensors of the batch ({tot_b / 1e9:.2f} GB fp32), FP64 NumPy oracle, {tot_s:.1f} s"}
+
+
+def run_batch(args):
+    import torch
+    from paper_1901_01652_gb300 import build, rtr
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    build.build()
+    rtr.lib()
+    shapes, Xs, Ks, Rs, cfg = batch_inputs(device)
+    N = 4
+    xbytes = sum(X.numel() * 4 for X in Xs)
+    # per-mode accounting: every projected mode's sketch reads X once, the
+    # first mode product reads it once more
+    mode_bytes = sum(X.numel() * 4 * (1 + sum(1 for k, d in zip(K, X.shape) if k < d)) for X, K in zip(Xs, Ks))
+    params = rtr.make_params(cfg["prec"], cfg["seed"], cfg["sweeps"])
+    b = rtr.rtr_batch_create(shapes, Ks, Rs, params, args.streams)
+    G = [[torch.empty(Rs[t][n] * shapes[t][n] * Rs[t][(n + 1) % N], dtype=torch.float64, device=device)
+          for n in range(N)] for t in range(len(shapes))]
+    rse = torch.empty(len(shapes), dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    t_first = time.perf_counter()
+    rtr.rtr_batch_run(b, Xs, G, rse, stream)            # eager run, tuning, capture
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t_first
+    for _ in range(max(0, args.warmup - 1)):
+        rtr.rtr_batch_run(b, Xs, G, rse, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            rtr.rtr_batch_run(b, Xs, G, rse, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = world * xbytes * args.steps / (ms * 1e-3) / 1e9
+    r = rse.cpu().numpy()
+    peak, peak_kind = measured_peak()
+    achieved = mode_bytes * args.steps / (ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "tensors": len(shapes), "total_gb": round(xbytes / 1e9, 3),
+                   "streams": args.streams, "prec": cfg["prec"], "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas{world}"},
+        "rse": {"mean": float(r.mean()), "max": float(r.max())},
+        "first_run_s": round(t_first, 3),
+        "gpu_launches": rtr.rtr_batch_graph_kernels(b) * args.steps,
+        "clocks": clk.summary(),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "kernel": "whole batched step (one graph), per-mode accounting of X reads"},
+    }
+    if not args.no_e2e:
+        Xh = [X.cpu().pin_memory() for X in Xs]
+        Gh = [[torch.empty(g.shape, dtype=torch.float64).pin_memory() for g in gt] for gt in G]
+        ek = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(ek):
+            for xd, xh in zip(Xs, Xh):
+                xd.copy_(xh, non_blocking=True)
+            rtr.rtr_batch_run(b, Xs, G, rse, stream)
+            for gt, ght in zip(G, Gh):
+                for g, gh in zip(gt, ght):
+                    gh.copy_(g, non_blocking=True)
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        d2h = sum(g.numel() * 8 for gt in G for g in gt)
+        out["e2e"] = {"value": round(world * xbytes * ek / el / 1e9, 3), "unit": "GB/s",
+                      "h2d_bytes_per_step": int(xbytes), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": round(el / ek * 1e3, 3)}
+        del Xh, Gh
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = batch_cpu_baseline(shapes, Ks, Rs, cfg)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    b.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch256":
+        run_batch(a)
     else:
         run_ours(a)

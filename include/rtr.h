@@ -212,6 +212,88 @@ int rtr_gaussian_table(int prec, double* out);
 int rtr_sketch_mode_noalloc(int prec, const void* X, int64_t A, int64_t I, int64_t B, int K,
                             uint64_t seed, int mode, double* Y, void* stream);
 
+/*
+ * Batched form: Algorithm 1 (sketch, orthonormal bases, projection chain,
+ * TR-ALS with the default start, back-projection, RSE) for `count` tensors of
+ * uneven shapes, run as one unit.
+ *
+ * rtr_batch_create: count >= 1 tensors of the same order N.  dims, K, R are
+ * HOST arrays of count*N entries (tensor t's entries at [t*N, t*N+N)), with
+ * the meaning they have in rtr_plan_create.  params applies to every tensor
+ * except the seed: tensor t uses seed params->seed + t (its own Omega_n and
+ * start cores); params->chain_order must be all -1 (each tensor takes its
+ * own default order).  nstreams (1..64): worker streams over which the
+ * tensors are spread (tensor t on worker t % nstreams).  The batch owns one
+ * plan and the step buffers (Y_n, Q_n, P, Z_n) per tensor.
+ *
+ * rtr_batch_run: X is a HOST array of count device pointers (tensor t:
+ * float64 for RTR_FP64, float32 otherwise, row-major of its dims); G a HOST
+ * array of count*N device float64 pointers (G[t*N+n]: R_n x I_n x R_{n+1});
+ * rse (may be NULL) a device float64[count] for the RSE of Section 4 of each
+ * tensor.  The first run with a given set of pointers executes eagerly
+ * (the mode-product autotuner times tile variants for shape classes it has
+ * not seen) and captures the same schedule into a CUDA graph; later runs
+ * with the same pointers replay that graph with one launch.  Asynchronous on
+ * `stream` (ordered after the work already on it), except that the first run
+ * with new pointers synchronises once before capturing.  Runs of one batch
+ * must not overlap in time.
+ */
+typedef struct rtr_batch rtr_batch;
+int rtr_batch_create(rtr_batch** batch, int count, int N, const int64_t* dims, const int* K,
+                     const int* R, const rtr_params* params, int nstreams);
+int rtr_batch_destroy(rtr_batch* batch);
+int rtr_batch_run(rtr_batch* batch, const void* const* X, double* const* G, double* rse, void* stream);
+/* number of kernel launches in the batch's captured graph (0 before the first run) */
+int rtr_batch_graph_kernels(const rtr_batch* batch, uint64_t* n);
+
+/*
+ * Learned proposer of the sketch sizes K_n and TR ranks R_n.  The paper sets
+ * K_n and R_n by hand for each experiment (Section 4); this is the library's
+ * own addition (it has no counterpart in the paper): a perceptron reads the
+ * singular-value spectra of the sketches Y_n = X_(n) Omega_n (Algorithm 1,
+ * step 5) and outputs (K_n, R_n) for up to 5 modes.
+ *
+ * Features (rtr_spectrum_features): for mode n < N, with s_0 >= s_1 >= ...
+ * the singular values of Y_n (I_n x Kf_n float64 row-major, device; 1 <=
+ * Kf_n <= 64), f[64 n + i] = max(0, 1 + log10(s_i / s_0) / 6) for
+ * i < min(I_n, Kf_n), else 0; rows n in [N, 5) are 0.  f: device float[320]
+ * (one feature row).  1 <= N <= 5.  The spectrum is taken from the
+ * eigenvalues of the float64 Gram matrix Y_n^T Y_n.
+ *
+ * Network: 320 -> 128 -> 128 -> 128 -> 10 with GELU (x Phi(x)) after the
+ * hidden layers.  theta: device float32[rtr_mlp_param_count()] =
+ * [W1 (128 x 320 row-major), b1[128], W2 (128 x 128), b2, W3 (128 x 128), b3,
+ * W4 (10 x 128), b4[10]] (float32 master weights).  Every matrix product
+ * rounds both operands to bfloat16 and accumulates in float32 on the tensor
+ * cores.  F: device float[batch x 320]; out: device float[batch x 10];
+ * 1 <= batch <= 65536.  work: device scratch of rtr_mlp_work_bytes(batch)
+ * bytes, owned by the caller (its first int holds status flags).
+ *
+ * rtr_mlp_grad: loss = 0.5 * sum(M .* (out - T)^2) / sum(M) for targets T
+ * and a 0/1 mask M (device float[batch x 10] each), written to *loss (device
+ * double, may be NULL); grad (device float, theta's layout) = d loss / d theta
+ * (no accumulation: overwritten).
+ * rtr_mlp_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step
+ * number `step` >= 1 on theta with moments m, v (device float, theta's
+ * layout, zero before step 1).
+ * rtr_mlp_status: synchronises the device, returns the work area's flags
+ * (RTR_FLAG_TIMEOUT if a bounded wait of a product gave up) and clears them.
+ * rtr_propose (host): out = one network output row (HOST float[10]) ->
+ * K_n = clamp(round(64 out[2n]), 1, min(I_n, 64)), R_n = clamp(round(16
+ * out[2n+1]), 1, r_max) for n < N (r_max <= 16), rounding half to even.
+ */
+size_t rtr_mlp_param_count(void);
+size_t rtr_mlp_work_bytes(int batch);
+int rtr_spectrum_features(int N, const int64_t* dims, const int* Kf, const double* const* Y, float* f,
+                          void* stream);
+int rtr_mlp_forward(const float* theta, const float* F, int batch, float* out, void* work, size_t work_bytes,
+                    void* stream);
+int rtr_mlp_grad(const float* theta, const float* F, const float* T, const float* M, int batch, float* grad,
+                 double* loss, void* work, size_t work_bytes, void* stream);
+int rtr_mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, void* stream);
+int rtr_mlp_status(void* work, int* flags);
+int rtr_propose(const float* out, int N, const int64_t* dims, int r_max, int* K, int* R);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,15 +5,18 @@
 // loads and stores go along the contiguous index).  Q (float64 in memory) is
 // staged in shared memory in the compute type, I in chunks of IC rows.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include "rtr_internal.cuh"
 
 namespace {
 
 constexpr int NT = 256;
-constexpr int TKO = 4;    // k per thread
-constexpr int TC = 2;     // columns per thread
 
-template <typename T>
+// TKO: output rows k per thread, TC: columns per thread (the tile variants
+// the autotuner chooses between)
+template <typename T, int TKO, int TC>
 __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_t A, int I, int64_t B,
                                                  const double* __restrict__ Q, int K, T* __restrict__ out,
                                                  int NKT, int CT, int IC, int64_t ntiles, int64_t nbt) {
@@ -90,35 +93,105 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
     }
 }
 
+template <typename T, int TKO, int TC>
+int launch_variant(rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, T* out,
+                   cudaStream_t s) {
+    int nkt = 1;
+    while (nkt * TKO < K) nkt *= 2;
+    const int CT = NT * TC / nkt;
+    if (CT < TC) return rtr_set_error(RTR_EINVAL, "mode product tile does not fit");
+    // I chunk: at most 128 (float64) / 256 (float32) rows, and the staged Q
+    // and X chunks within 100 KB so that two CTAs fit on an SM
+    const int64_t fit = (int64_t)(100 * 1024) / (int64_t)(sizeof(T) * (nkt * TKO + CT + 1));
+    const int IC = (int)std::max<int64_t>(1, std::min<int64_t>({I, sizeof(T) == 8 ? 128 : 256, fit}));
+    const size_t smem = sizeof(T) * ((size_t)IC * nkt * TKO + (size_t)IC * (CT + 1));
+    int64_t ntiles, nbt = 1;
+    if (B == 1) ntiles = rtr_ceil_div(A, CT);
+    else { nbt = rtr_ceil_div(B, CT); ntiles = A * nbt; }
+    auto kern = ttm_kernel<T, TKO, TC>;
+    RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 1;
+    RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)std::max(occ, 1) * p->num_sms));
+    kern<<<(unsigned)grid, NT, smem, s>>>(X, A, (int)I, B, Q, K, out, nkt, CT, IC, ntiles, nbt);
+    RTR_LAUNCH_CHECK("ttm_kernel");
+    return RTR_OK;
+}
+
+template <typename T>
+int run_variant(int v, rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, T* out,
+                cudaStream_t s) {
+    switch (v) {
+        case 0: return launch_variant<T, 4, 2>(p, X, A, I, B, Q, K, out, s);
+        case 1: return launch_variant<T, 2, 4>(p, X, A, I, B, Q, K, out, s);
+        case 2: return launch_variant<T, 4, 4>(p, X, A, I, B, Q, K, out, s);
+        default: return launch_variant<T, 8, 2>(p, X, A, I, B, Q, K, out, s);
+    }
+}
+constexpr int NVARIANTS = 4;
+
+// Autotuner: the first product of a shape class (type, I, K, layout of B)
+// outside stream capture times every tile variant on the call's own data
+// (CUDA events, synchronous) and caches the fastest; later calls, and calls
+// made while the stream is being captured, use the cache (variant 0 if the
+// class has not been tuned yet).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int, int>, int> g_tune;
+
+template <typename T>
+int tuned_ttm(rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, T* out,
+              cudaStream_t s) {
+    const auto key = std::make_tuple((int)sizeof(T), I, K, B == 1 ? 0 : (B < 64 ? 1 : 2));
+    int v = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) v = it->second;
+    }
+    if (v < 0) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        RTR_CUDA(cudaStreamIsCapturing(s, &cap));
+        if (cap != cudaStreamCaptureStatusNone || (double)A * I * B < 1e6) {
+            v = 0;   // not tuned: capturing, or too small for timing to matter
+        } else {
+            cudaEvent_t e0, e1;
+            RTR_CUDA(cudaEventCreate(&e0));
+            RTR_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            int bestv = 0;
+            for (int c = 0; c < NVARIANTS; ++c) {
+                int st = run_variant<T>(c, p, X, A, I, B, Q, K, out, s);      // warm-up
+                if (st) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+                RTR_CUDA(cudaEventRecord(e0, s));
+                st = run_variant<T>(c, p, X, A, I, B, Q, K, out, s);
+                RTR_CUDA(cudaEventRecord(e1, s));
+                RTR_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                RTR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; bestv = c; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            v = bestv;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[key] = v;
+        }
+    }
+    return run_variant<T>(v, p, X, A, I, B, Q, K, out, s);
+}
+
 }  // namespace
 
 int launch_ttm(rtr_plan* p, int is_f64, const void* X, int64_t A, int64_t I, int64_t B,
                const double* Q, int K, void* out, cudaStream_t s) {
     if (K < 1 || K > 64) return rtr_set_error(RTR_EINVAL, "mode product width %d out of range", K);
-    int nkt = 1;
-    while (nkt * TKO < K) nkt *= 2;
-    const int CT = NT * TC / nkt;
-    const size_t esz = is_f64 ? 8 : 4;
-    const int IC = (int)std::min<int64_t>(I, is_f64 ? 128 : 256);
-    const size_t smem = esz * ((size_t)IC * nkt * TKO + (size_t)IC * (CT + 1));
-    int64_t ntiles, nbt = 1;
-    if (B == 1) ntiles = rtr_ceil_div(A, CT);
-    else { nbt = rtr_ceil_div(B, CT); ntiles = A * nbt; }
-    int occ = 1;
-    if (is_f64) {
-        RTR_CUDA(cudaFuncSetAttribute(ttm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ttm_kernel<double>, NT, smem));
-    } else {
-        RTR_CUDA(cudaFuncSetAttribute(ttm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ttm_kernel<float>, NT, smem));
-    }
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)std::max(occ, 1) * p->num_sms));
-    if (is_f64)
-        ttm_kernel<double><<<(unsigned)grid, NT, smem, s>>>((const double*)X, A, (int)I, B, Q, K, (double*)out,
-                                                            nkt, CT, IC, ntiles, nbt);
-    else
-        ttm_kernel<float><<<(unsigned)grid, NT, smem, s>>>((const float*)X, A, (int)I, B, Q, K, (float*)out,
-                                                           nkt, CT, IC, ntiles, nbt);
-    RTR_LAUNCH_CHECK("ttm_kernel");
-    return RTR_OK;
+    if (is_f64) return tuned_ttm<double>(p, (const double*)X, A, I, B, Q, K, (double*)out, s);
+    return tuned_ttm<float>(p, (const float*)X, A, I, B, Q, K, (float*)out, s);
+}
+
+// the tile variant chosen for a shape class (-1 if not tuned), for tests
+int ttm_tuned_variant(int elem_size, int64_t I, int K, int bclass) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(elem_size, I, K, bclass));
+    return it == g_tune.end() ? -1 : it->second;
 }

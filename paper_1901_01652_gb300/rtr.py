@@ -24,7 +24,9 @@ ENTRY_POINTS = (
     "rtr_params_default", "rtr_last_error", "rtr_kernel_launches", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
     "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
-    "rtr_sketch_mode_noalloc",
+    "rtr_sketch_mode_noalloc", "rtr_batch_create", "rtr_batch_destroy", "rtr_batch_run",
+    "rtr_batch_graph_kernels", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
+    "rtr_mlp_forward", "rtr_mlp_grad", "rtr_mlp_adam", "rtr_mlp_status", "rtr_propose",
 )
 
 
@@ -76,6 +78,19 @@ def lib():
         "rtr_sketch_mode_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int64, ctypes.c_int64,
                                                    ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                                    _VP, _VP]),
+        "rtr_batch_create": (ctypes.c_int, [_VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _IP,
+                                            ctypes.POINTER(Params), ctypes.c_int]),
+        "rtr_batch_destroy": (ctypes.c_int, [_VP]),
+        "rtr_batch_run": (ctypes.c_int, [_VP, _VPP, _VPP, _VP, _VP]),
+        "rtr_batch_graph_kernels": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+        "rtr_mlp_param_count": (ctypes.c_size_t, []),
+        "rtr_mlp_work_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+        "rtr_spectrum_features": (ctypes.c_int, [ctypes.c_int, _I64P, _IP, _VPP, _VP, _VP]),
+        "rtr_mlp_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, _VP]),
+        "rtr_mlp_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+        "rtr_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP]),
+        "rtr_mlp_status": (ctypes.c_int, [_VP, _IP]),
+        "rtr_propose": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int, _I64P, ctypes.c_int, _IP, _IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -267,3 +282,118 @@ def rtr_sketch_mode_noalloc(prec, X, view, K, seed, mode, Y, stream=None):
     A, I, B = (int(v) for v in view)
     _check(lib().rtr_sketch_mode_noalloc(op, _ptr(X), A, I, B, int(K), int(seed), int(mode), _ptr(Y),
                                          _stream(stream)))
+
+
+class Batch:
+    """Owning handle of an rtr_batch."""
+
+    def __init__(self, handle, shapes, K, R, params):
+        self.handle = handle
+        self.shapes = [tuple(int(d) for d in s) for s in shapes]
+        self.count = len(self.shapes)
+        self.N = len(self.shapes[0])
+        self.K = [tuple(int(k) for k in ks) for ks in K]
+        self.R = [tuple(int(r) for r in rs) for rs in R]
+        self.params = params
+        self.x_dtype = torch.float64 if params.prec == RTR_FP64 else torch.float32
+
+    def close(self):
+        if self.handle:
+            lib().rtr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rtr_batch_create(shapes, K, R, params, nstreams=8):
+    """shapes, K, R: one sequence of N values per tensor."""
+    N = len(shapes[0])
+    if any(len(s) != N for s in list(shapes) + list(K) + list(R)) or not (len(shapes) == len(K) == len(R)):
+        raise ValueError("every tensor needs N dims, K and R values")
+    h = _VP()
+    flat = lambda xs: [v for s in xs for v in s]
+    _check(lib().rtr_batch_create(ctypes.byref(h), len(shapes), N, _i64(flat(shapes)), _i32(flat(K)),
+                                  _i32(flat(R)), ctypes.byref(params), int(nstreams)))
+    return Batch(h, shapes, K, R, params)
+
+
+def rtr_batch_destroy(batch):
+    batch.close()
+
+
+def rtr_batch_run(batch, X, G, rse=None, stream=None):
+    """X: list of count device tensors; G: list of count lists of N float64 core buffers."""
+    if len(X) != batch.count or len(G) != batch.count:
+        raise ValueError("X and G need one entry per tensor")
+    xs = _ptrs(X, batch.x_dtype, "X")
+    gs = _ptrs([g for gt in G for g in gt], torch.float64, "G")
+    _dev(rse, torch.float64, "rse")
+    _check(lib().rtr_batch_run(batch.handle, xs, gs, _ptr(rse), _stream(stream)))
+
+
+def rtr_batch_graph_kernels(batch):
+    n = ctypes.c_uint64(0)
+    _check(lib().rtr_batch_graph_kernels(batch.handle, ctypes.byref(n)))
+    return int(n.value)
+
+
+# ----------------------------------------------------------------------------- learned proposer
+
+def rtr_mlp_param_count():
+    return int(lib().rtr_mlp_param_count())
+
+
+def rtr_mlp_work_bytes(batch):
+    return int(lib().rtr_mlp_work_bytes(int(batch)))
+
+
+def rtr_spectrum_features(dims, Kf, Y, f, stream=None):
+    """Y: list of N float64 sketches (I_n x Kf_n); f: float32 device tensor of 320."""
+    _dev(f, torch.float32, "f")
+    _check(lib().rtr_spectrum_features(len(dims), _i64(dims), _i32(Kf), _ptrs(Y, torch.float64, "Y"), _ptr(f),
+                                       _stream(stream)))
+
+
+def rtr_mlp_forward(theta, F, out, work, stream=None):
+    for t, n in ((theta, "theta"), (F, "F"), (out, "out")):
+        _dev(t, torch.float32, n)
+    _dev(work, None, "work")
+    batch = F.shape[0]
+    _check(lib().rtr_mlp_forward(_ptr(theta), _ptr(F), int(batch), _ptr(out), _ptr(work),
+                                 work.numel() * work.element_size(), _stream(stream)))
+
+
+def rtr_mlp_grad(theta, F, T, M, grad, loss, work, stream=None):
+    for t, n in ((theta, "theta"), (F, "F"), (T, "T"), (M, "M"), (grad, "grad")):
+        _dev(t, torch.float32, n)
+    _dev(loss, torch.float64, "loss")
+    _dev(work, None, "work")
+    _check(lib().rtr_mlp_grad(_ptr(theta), _ptr(F), _ptr(T), _ptr(M), int(F.shape[0]), _ptr(grad), _ptr(loss),
+                              _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def rtr_mlp_adam(theta, grad, m, v, step, lr, stream=None):
+    for t, n in ((theta, "theta"), (grad, "grad"), (m, "m"), (v, "v")):
+        _dev(t, torch.float32, n)
+    _check(lib().rtr_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)))
+
+
+def rtr_mlp_status(work):
+    f = ctypes.c_int(0)
+    st = lib().rtr_mlp_status(_ptr(_dev(work, None, "work")), ctypes.byref(f))
+    _check(st)
+    return f.value
+
+
+def rtr_propose(out_row, dims, r_max=16):
+    """out_row: 10 host floats -> (K list, R list)."""
+    o = (ctypes.c_float * 10)(*[float(x) for x in out_row])
+    N = len(dims)
+    K = (ctypes.c_int * N)()
+    R = (ctypes.c_int * N)()
+    _check(lib().rtr_propose(o, N, _i64(dims), int(r_max), K, R))
+    return list(K), list(R)

@@ -22,6 +22,9 @@ CONFIGS = {
                           sweeps=30, prec="bf16", seed=1903),
     "c3_fp8_hsi": dict(dims=(1024, 1024, 256), n_sig=20, n_bumps=40, noise_rel=0.01,
                        K=(60, 60, 30), eps=1e-2, prec="fp8", seed=1904),
+    # 256 image-like order-4 tensors (H, W, C, S), modes U{32..96}, TR rank
+    # r ~ U{4..12} per tensor, K_n = min(I_n, 2r), R_n = r
+    "c4_batch256": dict(count=256, lo=32, hi=96, rlo=4, rhi=12, sweeps=20, prec="bf16", seed=1905),
 }
 
 
@@ -89,3 +92,25 @@ def batch_shapes(count=256, lo=32, hi=96, rlo=4, rhi=12, seed=1905):
         dims = tuple(int(x) for x in rng.integers(lo, hi + 1, size=4))
         out.append((dims, int(rng.integers(rlo, rhi + 1))))
     return out
+
+
+def smoothed_tr_cores(dims, r, seed, sigma=2.0, spatial=(0, 1)):
+    """TR cores with N(0, 1) entries, those of the `spatial` modes smoothed
+    along their index by a Gaussian filter (std `sigma` samples), so that the
+    tensor varies smoothly along those modes like image rows and columns."""
+    from scipy.ndimage import gaussian_filter1d
+    cores = tr_cores(dims, r, seed)
+    return [gaussian_filter1d(c, sigma, axis=1, mode="nearest") if n in spatial else c
+            for n, c in enumerate(cores)]
+
+
+def to_pixels(x):
+    """Min-max map to [0, 255] and round to integers (numpy array or torch
+    tensor, same type back)."""
+    lo, hi = x.min(), x.max()
+    return ((x - lo) * (255.0 / (hi - lo))).round()
+
+
+def batch_ranks(dims, r):
+    """Sketch sizes and TR ranks of one batch tensor: K_n = min(I_n, 2r), R_n = r."""
+    return tuple(min(int(d), 2 * r) for d in dims), (r,) * len(dims)
