@@ -43,9 +43,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batch256"],
-                    help="c2 = the 200^4 tensor (default); batch256 = 256 uneven image-like tensors")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch256", "c1", "c3"],
+                    help="c2 = the 200^4 tensor (default); batch256 = 256 uneven image-like tensors; "
+                         "c1 = FP64 60^4 TR-ALS; c3 = hyperspectral-shaped 1024x1024x256 TR-SVD")
     ap.add_argument("--streams", type=int, default=16, help="worker streams of the batched form")
+    ap.add_argument("--batch-count", type=int, default=256, help="tensors of the batched workload (256 = the named workload)")
+    ap.add_argument("--no-graph", action="store_true", help="batched form: eager runs, no CUDA graph")
     return ap.parse_args()
 
 
@@ -117,13 +120,16 @@ def measured_peak():
 
 def ncu_traffic(kernel_key):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel build (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    summary (profiles/traffic.txt: "<key> <bytes>" lines), else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        d = json.load(open(p))
-        return d.get(kernel_key)
+        for line in open(p):
+            parts = line.split()
+            if len(parts) == 2 and parts[0] == kernel_key:
+                return int(parts[1])
     except Exception:
-        return None
+        pass
+    return None
 
 
 def build_input(dims, rank, snr_db, seed, device):
@@ -434,13 +440,15 @@ def run_batch(args):
     torch.cuda.set_device(device)
     build.build()
     rtr.lib()
-    shapes, Xs, Ks, Rs, cfg = batch_inputs(device)
+    shapes, Xs, Ks, Rs, cfg = batch_inputs(device, args.batch_count)
     N = 4
     xbytes = sum(X.numel() * 4 for X in Xs)
     # per-mode accounting: every projected mode's sketch reads X once, the
     # first mode product reads it once more
     mode_bytes = sum(X.numel() * 4 * (1 + sum(1 for k, d in zip(K, X.shape) if k < d)) for X, K in zip(Xs, Ks))
     params = rtr.make_params(cfg["prec"], cfg["seed"], cfg["sweeps"])
+    if args.no_graph:
+        params.flags = rtr.PARAM_NO_GRAPH
     b = rtr.rtr_batch_create(shapes, Ks, Rs, params, args.streams)
     G = [[torch.empty(Rs[t][n] * shapes[t][n] * Rs[t][(n + 1) % N], dtype=torch.float64, device=device)
           for n in range(N)] for t in range(len(shapes))]
@@ -469,8 +477,9 @@ def run_batch(args):
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "tensors": len(shapes), "total_gb": round(xbytes / 1e9, 3),
-                   "streams": args.streams, "prec": cfg["prec"], "l2": "inputs larger than L2 (no flush)",
+        "config": {"workload": BATCH_WORKLOAD if len(shapes) == 256 else f"first {len(shapes)} tensors of: " + BATCH_WORKLOAD,
+                   "tensors": len(shapes), "total_gb": round(xbytes / 1e9, 3),
+                   "streams": args.streams, "graph": not args.no_graph, "prec": cfg["prec"], "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas{world}"},
         "rse": {"mean": float(r.mean()), "max": float(r.max())},
         "first_run_s": round(t_first, 3),
@@ -507,11 +516,164 @@ def run_batch(args):
     b.close()
 
 
+# ----------------------------------------------------------------------------- other single-tensor workloads
+
+SINGLE = {
+    "c1": dict(workload="rTR-ALS order-4 60^4 fp64 (104 MB), TR rank 5 + 40 dB noise, K=15, R=5, 20 sweeps",
+               dims=(60, 60, 60, 60), K=(15,) * 4, R=(5,) * 4, prec="fp64", method="als", sweeps=20,
+               eps=None, seed=1902, sample=(30, 30, 30, 30)),
+    "c3": dict(workload="rTR-SVD hyperspectral-shaped 1024x1024x256 fp32 (1.07 GB), 20 abundance maps x 20 "
+                        "spectra + 1% noise, K=(60,60,30), eps=1e-2, BF16 sketch",
+               dims=(1024, 1024, 256), K=(60, 60, 30), R=(16, 16, 16), prec="bf16", method="svd", sweeps=1,
+               eps=1e-2, seed=1904, sample=(256, 256, 64)),
+}
+
+
+def single_input(name, dims, seed, device, host=False):
+    """The named workload's tensor (CUDA tensor, or float64 NumPy on the host
+    for the oracle's sample)."""
+    import torch
+    from paper_1901_01652_gb300 import rtr, workloads
+    if name == "c1":
+        cores = workloads.tr_cores(dims, 5, seed)
+        if host:
+            from oracle import tensor as ot
+            S = ot.tr_full(cores)
+            return S + workloads.snr_sigma(ot.fro(S), S.size, 40.0) * workloads.unit_noise(dims, seed)
+        R = [5] * len(dims)
+        X = torch.empty(dims, dtype=torch.float64, device=device)
+        work = torch.empty(rtr.rtr_reconstruct_work_bytes(dims, R), dtype=torch.uint8, device=device)
+        rtr.rtr_reconstruct(dims, R, [torch.from_numpy(c).to(device) for c in cores], "fp64", X, work)
+        nrm = float(torch.linalg.vector_norm(X))
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        X.add_(torch.randn(dims, generator=g, device=device, dtype=torch.float64),
+               alpha=workloads.snr_sigma(nrm, X.numel(), 40.0))
+        return X
+    H, W, B = dims
+    A, Sg = workloads.hsi_factors(H, W, B, n_sig=20, n_bumps=40, seed=seed)
+    if host:
+        X = np.einsum("hws,bs->hwb", A, Sg)
+        return X + 0.01 * np.linalg.norm(X) / np.sqrt(X.size) * workloads.unit_noise(X.shape, seed)
+    X = (torch.from_numpy(A.reshape(-1, A.shape[-1])).to(device) @ torch.from_numpy(Sg.T).to(device))
+    X = X.reshape(dims)
+    nrm = float(torch.linalg.vector_norm(X))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    X.add_(torch.randn(dims, generator=g, device=device, dtype=torch.float64), alpha=0.01 * nrm / X.numel() ** 0.5)
+    return X.float().contiguous()
+
+
+def single_step(eng, X, spec, stream):
+    eng.sketch(X, stream)
+    eng.project(X, stream)
+    if spec["method"] == "als":
+        eng.als(None, stream)
+    else:
+        eng.svd(spec["eps"], None, stream)
+    eng.backproject(stream)
+    eng.compute_rse(stream)
+
+
+def run_single(args):
+    import torch
+    from paper_1901_01652_gb300 import build, rtr
+    from paper_1901_01652_gb300.api import RTRD, decompose
+    spec = SINGLE[args.workload]
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    build.build()
+    rtr.lib()
+    X = single_input(args.workload, spec["dims"], spec["seed"], device)
+    xbytes = X.numel() * X.element_size()
+    eng = RTRD(spec["dims"], spec["K"], spec["R"], spec["prec"], spec["seed"], spec["sweeps"],
+               spec["eps"] or 1e-2, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        single_step(eng, X, spec, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = rtr.rtr_kernel_launches()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            single_step(eng, X, spec, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = rtr.rtr_kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    value = world * xbytes * args.steps / (ms * 1e-3) / 1e9
+    # sketch alone (one launch set per step) for the roofline of the sketch kernels
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.steps):
+        eng.sketch(X, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    nproj = sum(1 for k, d in zip(eng.plan.K, spec["dims"]) if k < d)
+    sk_ms = s0.elapsed_time(s1) / args.steps / max(nproj, 1)
+    peak, peak_kind = measured_peak()
+    achieved = xbytes / (sk_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if spec["prec"] == "fp64" else "bf16",
+        "data": "synthetic",
+        "config": {"workload": spec["workload"], "dims": list(spec["dims"]), "K": list(spec["K"]),
+                   "prec": spec["prec"], "method": spec["method"], "l2": "inputs larger than L2 (no flush)"
+                   if xbytes > 129e6 else "input smaller than L2 (resident between steps)",
+                   "parallelism": f"replicas{world}"},
+        "rse": float(eng.rse.cpu()[0]), "ranks": list(eng.ranks),
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "roofline": {"bound": "alu" if spec["prec"] == "fp64" else "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": None, "kernel": f"sketch_{spec['prec']}_{args.workload} (mean per mode)",
+                     "sketch_ms_per_mode": round(sk_ms, 4)},
+    }
+    if not args.no_e2e:
+        Xh = X.cpu().pin_memory()
+        decompose(Xh, spec["K"], spec["R"], spec["method"], spec["prec"], spec["seed"], spec["sweeps"],
+                  spec["eps"] or 1e-2, engine=eng)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ek = max(1, min(args.steps, 3))
+        for _ in range(ek):
+            G, _, _ = decompose(Xh, spec["K"], spec["R"], spec["method"], spec["prec"], spec["seed"],
+                                spec["sweeps"], spec["eps"] or 1e-2, engine=eng)
+        el = time.perf_counter() - t
+        out["e2e"] = {"value": round(world * xbytes * ek / el / 1e9, 3), "unit": "GB/s",
+                      "h2d_bytes_per_step": int(xbytes), "d2h_bytes_per_step": int(sum(g.numel() * 8 for g in G) + 8),
+                      "ms_per_step": round(el / ek * 1e3, 3)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import rtrd as orc
+        from oracle import tensor as ot
+        Xs = single_input(args.workload, spec["sample"], spec["seed"], None, host=True)
+        if spec["prec"] != "fp64":
+            Xs = Xs.astype(np.float32).astype(np.float64)
+        t = time.perf_counter()
+        ref = orc.rtrd(Xs, spec["K"], spec["R"], spec["method"], seed=spec["seed"], prec=spec["prec"],
+                       sweeps=spec["sweeps"], eps=spec["eps"])
+        if spec["method"] == "als":
+            orc.rse_identity(ot.fro(Xs) ** 2, ref["P"], ref["Z"])
+        el = time.perf_counter() - t
+        b = Xs.size * (8 if spec["prec"] == "fp64" else 4)
+        out["cpu_baseline"] = {"value": round(b / el / 1e9, 6), "unit": "GB/s", "cores": os.cpu_count(),
+                               "kind": "oracle", "sample": f"{'x'.join(map(str, spec['sample']))} tensor of the same "
+                                                            f"recipe, FP64 NumPy oracle, {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch256":
         run_batch(a)
+    elif a.workload in SINGLE:
+        run_single(a)
     else:
         run_ours(a)

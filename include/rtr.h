@@ -50,6 +50,9 @@ extern "C" {
 #define RTR_FP32  1   /* X float32; SIMT float32 sketch / chain, float64 QR & solves */
 #define RTR_BF16  2   /* X float32; tcgen05 BF16 (hi+lo split) sketch / chain      */
 
+/* rtr_params.flags bits */
+#define RTR_PARAM_NO_GRAPH     1   /* rtr_batch_run: always run eagerly, never capture a graph */
+
 /* device flag bits (rtr_plan_flags) */
 #define RTR_FLAG_NONFINITE     1   /* NaN/Inf met in an input or a reduction */
 #define RTR_FLAG_QR_FALLBACK   2   /* CholeskyQR2 failed; Householder QR used */
@@ -63,7 +66,7 @@ typedef struct {
     uint64_t seed;            /* seed of the Gaussian test matrices Omega_n */
     int      sweeps;          /* TR-ALS sweeps (each updates cores 1..N once) */
     double   tol;             /* TR-SVD relative tolerance epsilon */
-    int      flags;           /* reserved, 0 */
+    int      flags;           /* RTR_PARAM_* bits, 0 = defaults */
     int      chain_order[8];  /* order of the mode products of step 7; all -1 = default
                                  (largest I_n/K_n first, ties to the later mode) */
 } rtr_params;
@@ -131,7 +134,8 @@ int rtr_project(rtr_plan* plan, const void* X, const double* const* Y,
  * otherwise the library writes its default start (discrete-Gaussian cores
  * from Philox4x64-10 with key (seed + 1, 256 + n), scaled so ||TR(Z)|| = ||P||).
  * err: device float64[sweeps] (may be NULL) receives ||P - TR(Z)||_F after
- * each sweep.
+ * each sweep.  Requires R_n R_{n+1} <= 144 for every n (else
+ * RTR_EUNSUPPORTED).
  */
 int rtr_als(rtr_plan* plan, const void* P, double* const* Z, int init_given,
             double* err, void* stream);
@@ -233,7 +237,9 @@ int rtr_sketch_mode_noalloc(int prec, const void* X, int64_t A, int64_t I, int64
  * tensor.  The first run with a given set of pointers executes eagerly
  * (the mode-product autotuner times tile variants for shape classes it has
  * not seen) and captures the same schedule into a CUDA graph; later runs
- * with the same pointers replay that graph with one launch.  Asynchronous on
+ * with the same pointers replay that graph with one launch (with
+ * RTR_PARAM_NO_GRAPH in params->flags every run is eager and nothing is
+ * captured, for one-shot batches).  Asynchronous on
  * `stream` (ordered after the work already on it), except that the first run
  * with new pointers synchronises once before capturing.  Runs of one batch
  * must not overlap in time.
@@ -243,6 +249,9 @@ int rtr_batch_create(rtr_batch** batch, int count, int N, const int64_t* dims, c
                      const int* R, const rtr_params* params, int nstreams);
 int rtr_batch_destroy(rtr_batch* batch);
 int rtr_batch_run(rtr_batch* batch, const void* const* X, double* const* G, double* rse, void* stream);
+/* device flags (RTR_FLAG_*) raised by the batch's runs so far, ORed over its
+ * tensors; synchronises the device and clears them */
+int rtr_batch_flags(rtr_batch* batch, int* flags);
 /* number of kernel launches in the batch's captured graph (0 before the first run) */
 int rtr_batch_graph_kernels(const rtr_batch* batch, uint64_t* n);
 
@@ -267,7 +276,8 @@ int rtr_batch_graph_kernels(const rtr_batch* batch, uint64_t* n);
  * rounds both operands to bfloat16 and accumulates in float32 on the tensor
  * cores.  F: device float[batch x 320]; out: device float[batch x 10];
  * 1 <= batch <= 65536.  work: device scratch of rtr_mlp_work_bytes(batch)
- * bytes, owned by the caller (its first int holds status flags).
+ * bytes, owned by the caller; its first int holds status flags and must be
+ * zero before the first call (rtr_mlp_status clears it).
  *
  * rtr_mlp_grad: loss = 0.5 * sum(M .* (out - T)^2) / sum(M) for targets T
  * and a 0/1 mask M (device float[batch x 10] each), written to *loss (device

@@ -16,6 +16,7 @@
 #include <type_traits>
 #include "rtr_internal.cuh"
 #include "dense.cuh"
+#include "als_tile.cuh"
 
 size_t contract_partial_elems(int num_sms, int64_t I, int C);
 
@@ -119,6 +120,7 @@ struct AlsContractArgs {
     int N, n;
     int64_t Jpre;
     double* partial;
+    int stage;                        // 1: the other cores are copied to shared memory first
 };
 
 constexpr int ALS_LB = 16;          // last-mode indices per block
@@ -136,14 +138,33 @@ __global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs
     const int Rl = a.R[ml];                         // left rank of the last core
     T* M0 = reinterpret_cast<T*>(smem_raw);          // Rb x 16
     T* M1 = M0 + Rb * RTR_MAX_RANK;                  // Rb x 16
-    T* S = M1 + Rb * RTR_MAX_RANK;                   // ALS_LB x C
-    T* Pv = S + ALS_LB * C;                          // ALS_LB x Kn
+    const int Cp = rtr::tile_cp(C);
+    T* S = M1 + Rb * RTR_MAX_RANK;                   // ALS_LB x Cp
+    T* Pv = S + ALS_LB * Cp;                         // ALS_LB x Kn
     const T* P = reinterpret_cast<const T*>(a.P);
     const int tid = threadIdx.x;
-    const int nout = Kn * C;
-    T acc[ALS_MAXACC];
-#pragma unroll
-    for (int q = 0; q < ALS_MAXACC; ++q) acc[q] = T(0);
+    // the other cores, read many times per prefix: shared memory (if they fit)
+    // instead of chains of dependent global loads
+    const T* Zc[RTR_MAXN];
+    {
+        T* zs = Pv + ALS_LB * Kn;
+        for (int t = 1; t < N; ++t) {
+            const int m = a.cyc[t];
+            const T* src = reinterpret_cast<const T*>(a.Z[m]);
+            if (a.stage) {
+                const int cnt = (int)(a.R[m] * a.K[m] * a.R[(m + 1) % N]);
+                for (int e = tid; e < cnt; e += blockDim.x) zs[e] = src[e];
+                Zc[m] = zs;
+                zs += cnt;
+            } else {
+                Zc[m] = src;
+            }
+        }
+        __syncthreads();
+    }
+    const rtr::WTile wt = rtr::wtile(C, Kn);
+    T acc[rtr::TILE_IP][4];
+    rtr::wtile_zero(acc);
 
     for (int64_t jp = blockIdx.x; jp < a.Jpre; jp += gridDim.x) {
         // decode the prefix (row-major over c_1 .. c_{N-2}) and its P offset
@@ -162,7 +183,7 @@ __global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs
             const int Rc = a.R[(m + 1) % N];
             for (int e = tid; e < Rb * Rc; e += blockDim.x) {
                 const int be = e / Rc, g = e % Rc;
-                M0[be * RTR_MAX_RANK + g] = reinterpret_cast<const T*>(a.Z[m])[((int64_t)be * a.K[m] + idx[1]) * Rc + g];
+                M0[be * RTR_MAX_RANK + g] = Zc[m][((int64_t)be * a.K[m] + idx[1]) * Rc + g];
             }
         }
         T* cur = M0;
@@ -175,7 +196,7 @@ __global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs
                 const int be = e / Rc, g = e % Rc;
                 T sum = T(0);
                 for (int c = 0; c < Rm; ++c)
-                    sum = fma(cur[be * RTR_MAX_RANK + c], reinterpret_cast<const T*>(a.Z[m])[((int64_t)c * a.K[m] + idx[t]) * Rc + g], sum);
+                    sum = fma(cur[be * RTR_MAX_RANK + c], Zc[m][((int64_t)c * a.K[m] + idx[t]) * Rc + g], sum);
                 nxt[be * RTR_MAX_RANK + g] = sum;
             }
             T* tmp = cur; cur = nxt; nxt = tmp;
@@ -183,41 +204,28 @@ __global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs
         __syncthreads();
         for (int l0 = 0; l0 < Kl; l0 += ALS_LB) {
             const int lb = min(ALS_LB, Kl - l0);
-            // S[l][(beta, alpha)] = sum_g M[beta][g] Z_last[g, l0 + l, alpha]
-            for (int e = tid; e < ALS_LB * C; e += blockDim.x) {
-                const int l = e / C, c = e % C;
+            // S[l][(beta, alpha)] = sum_g M[beta][g] Z_last[g, l0 + l, alpha]  (zero padding to Cp)
+            for (int e = tid; e < lb * Cp; e += blockDim.x) {
+                const int l = e / Cp, c = e % Cp;
                 T sum = T(0);
-                if (l < lb) {
+                if (c < C) {
                     const int be = c / Rn, al = c % Rn;
-                    for (int g = 0; g < Rl; ++g)
-                        sum = fma(cur[be * RTR_MAX_RANK + g], reinterpret_cast<const T*>(a.Z[ml])[((int64_t)g * Kl + l0 + l) * Rn + al], sum);
+                    const T* zl = Zc[ml] + (int64_t)(l0 + l) * Rn + al;
+                    const int64_t zs = (int64_t)Kl * Rn;
+                    for (int g = 0; g < Rl; ++g) sum = fma(cur[be * RTR_MAX_RANK + g], zl[g * zs], sum);
                 }
                 S[e] = sum;
             }
-            for (int e = tid; e < ALS_LB * Kn; e += blockDim.x) {
+            for (int e = tid; e < lb * Kn; e += blockDim.x) {
                 const int l = e / Kn, i = e % Kn;
-                Pv[e] = (l < lb) ? P[base + (int64_t)(l0 + l) * a.stride[ml] + (int64_t)i * a.stride[n]] : T(0);
+                Pv[e] = P[base + (int64_t)(l0 + l) * a.stride[ml] + (int64_t)i * a.stride[n]];
             }
             __syncthreads();
-#pragma unroll
-            for (int q = 0; q < ALS_MAXACC; ++q) {
-                const int e = tid + q * 256;
-                if (e < nout) {
-                    const int i = e / C, c = e % C;
-                    T sum = acc[q];
-#pragma unroll 4
-                    for (int l = 0; l < ALS_LB; ++l) sum = fma(Pv[l * Kn + i], S[l * C + c], sum);
-                    acc[q] = sum;
-                }
-            }
+            rtr::wtile_accum(acc, wt, Pv, Kn, S, Cp, lb);
             __syncthreads();
         }
     }
-#pragma unroll
-    for (int q = 0; q < ALS_MAXACC; ++q) {
-        const int e = tid + q * 256;
-        if (e < nout) a.partial[(int64_t)blockIdx.x * nout + e] = (double)acc[q];
-    }
+    rtr::wtile_store(acc, wt, Kn, C, a.partial + (int64_t)blockIdx.x * Kn * C);
 }
 
 // W[e] = sum of the CTA partials (one warp per output, fixed order)
@@ -753,6 +761,10 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     double* normP2 = p->scal + 1;
     double* normTR2 = p->scal + 2;
 
+    for (int n = 0; n < N; ++n)
+        if (p->R[n] * p->R[(n + 1) % N] > 144)
+            return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: R_%d R_%d = %d > 144", n, (n + 1) % N,
+                                 p->R[n] * p->R[(n + 1) % N]);
     int st = launch_sumsq(P, is_f64, p->pnumel, p->partial, 1024, normP2, s);
     if (st) return st;
 
@@ -858,7 +870,16 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             if (nout > 256 * ALS_MAXACC) return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: K_n R_n R_{n+1} > 10240");
             int64_t gx = std::min<int64_t>(ca.Jpre, 4 * (int64_t)p->num_sms);
             gx = std::min<int64_t>(gx, (int64_t)(p->partial_elems / nout));
-            const size_t csmem = sizeof(T) * (2 * (size_t)Rn1 * RTR_MAX_RANK + (size_t)ALS_LB * C + (size_t)ALS_LB * I);
+            size_t csmem = sizeof(T) * (2 * (size_t)Rn1 * RTR_MAX_RANK + (size_t)ALS_LB * ((C + 3) & ~3) + (size_t)ALS_LB * I);
+            size_t zbytes = 0;
+            for (int t = 1; t < N; ++t) {
+                const int m = (n + t) % N;
+                zbytes += sizeof(T) * (size_t)p->R[m] * Kd[m] * p->R[(m + 1) % N];
+            }
+            ca.stage = (csmem + zbytes <= 96 * 1024) ? 1 : 0;
+            if (ca.stage) csmem += zbytes;
+            if (csmem > 48 * 1024)
+                RTR_CUDA(cudaFuncSetAttribute(als_contract_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
             als_contract_kernel<T><<<(unsigned)gx, 256, csmem, s>>>(ca);
             RTR_LAUNCH_CHECK("als_contract_kernel");
             als_reduce_kernel<<<(unsigned)rtr_ceil_div((int64_t)nout * 32, 256), 256, 0, s>>>(p->partial, (int)gx, nout, W);

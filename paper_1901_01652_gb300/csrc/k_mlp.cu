@@ -411,6 +411,7 @@ int rtr_mlp_status(void* work, int* flags) {
     RTR_CUDA(cudaDeviceSynchronize());
     RTR_CUDA(cudaMemcpy(flags, work, sizeof(int), cudaMemcpyDeviceToHost));
     RTR_CUDA(cudaMemset(work, 0, sizeof(int)));
+    *flags &= RTR_FLAG_TIMEOUT;
     return *flags & RTR_FLAG_TIMEOUT ? RTR_ETIMEOUT : RTR_OK;
 }
 

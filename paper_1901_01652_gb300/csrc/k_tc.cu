@@ -24,6 +24,31 @@
 
 namespace {
 
+// Position of a role's local step t in a ring of S slots (slot = t mod S,
+// use = t div S), advanced without divisions: 64-bit integer division is a
+// long subroutine, far too slow for a per-chunk loop.
+struct Ring {
+    int slot = 0, S = 1;
+    uint32_t use = 0;
+    __device__ explicit Ring(int S_, int t0 = 0) : S(S_) { step(t0); }
+    __device__ void step(int by) {
+        slot += by;
+        while (slot >= S) { slot -= S; ++use; }
+    }
+};
+
+// (a, b-chunk) of chunk ch = a * nbc + bi, for ch = ch0, ch0 + stride, ...
+struct ChunkPos {
+    int64_t a, bi, qa, qb, nbc;
+    __device__ ChunkPos(int64_t ch0, int64_t stride, int64_t nbc_) : nbc(nbc_) {
+        a = ch0 / nbc; bi = ch0 % nbc; qa = stride / nbc; qb = stride % nbc;
+    }
+    __device__ void step() {
+        bi += qb; a += qa;
+        if (bi >= nbc) { bi -= nbc; ++a; }
+    }
+};
+
 using namespace rtr::tc;
 
 constexpr int CONV_WARPS = 8;
@@ -103,16 +128,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
     if (warp < CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
-        for (int64_t t = 0; t < nloc; ++t) {
+        Ring rg(S);
+        ChunkPos cp(blockIdx.x, gridDim.x, p.nbc);
+        for (int64_t t = 0; t < nloc; ++t, rg.step(1), cp.step()) {
             const int64_t ch = blockIdx.x + t * gridDim.x;
-            const int s = (int)(t % S);
-            const uint32_t u = (uint32_t)(t / S);
+            const int s = rg.slot;
+            const uint32_t u = rg.use;
             if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
             const uint32_t hi_base = stage0 + s * stage_bytes;
             const uint32_t lo_base = hi_base + a_bytes;
             float csum = 0.f;
             if (p.B > 1) {
-                const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * KC;
+                const int64_t a = cp.a, b0 = cp.bi * KC;
                 const int len = (int)min((int64_t)KC, p.B - b0);
                 const float* xrow0 = p.X + ((int64_t)a * p.I + rbeg) * p.B + b0;
                 if (p.vec && len == KC) {
@@ -215,14 +242,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
         // ================================================================ Omega generators
         const int kk = tid - CONV_THREADS;            // 0..63: the r column this thread fills
         const int ncall = (p.K + 19) / 20;
-        for (int64_t t = 0; t < nloc; ++t) {
+        Ring rg(S);
+        ChunkPos cp(blockIdx.x, gridDim.x, p.nbc);
+        for (int64_t t = 0; t < nloc; ++t, rg.step(1), cp.step()) {
             const int64_t ch = blockIdx.x + t * gridDim.x;
-            const int s = (int)(t % S);
-            const uint32_t u = (uint32_t)(t / S);
+            const int s = rg.slot;
+            const uint32_t u = rg.use;
             int64_t r0;
             int len;
             if (p.B > 1) {
-                const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * KC;
+                const int64_t a = cp.a, b0 = cp.bi * KC;
                 r0 = a * p.B + b0;
                 len = (int)min((int64_t)KC, p.B - b0);
             } else {
@@ -249,9 +278,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
     } else {
         // ================================================================ MMA issuer
         const uint32_t idesc = idesc_bf16_f32(128, p.N);
-        for (int64_t t = 0; t < nloc; ++t) {
-            const int s = (int)(t % S);
-            const uint32_t u = (uint32_t)(t / S);
+        Ring rg(S);
+        for (int64_t t = 0; t < nloc; ++t, rg.step(1)) {
+            const int s = rg.slot;
+            const uint32_t u = rg.use;
             if (!mbar_wait(&fullA[s], u & 1, abort, p.flags)) break;
             if (!mbar_wait(&fullB[s], u & 1, abort, p.flags)) break;
             tc_fence_after();
@@ -430,9 +460,10 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     if (warp < TM_CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
-        for (int64_t t = 0; t < nloc; ++t) {
-            const int ss = (int)(t % S_st), so = (int)(t % S_op);
-            const uint32_t us = (uint32_t)(t / S_st), uo = (uint32_t)(t / S_op);
+        Ring rs(S_st), ro(S_op);
+        for (int64_t t = 0; t < nloc; ++t, rs.step(1), ro.step(1)) {
+            const int ss = rs.slot, so = ro.slot;
+            const uint32_t us = rs.use, uo = ro.use;
             if (!mbar_wait(&stfull[ss], us & 1, abort, p.flags)) break;
             if (t >= S_op && !mbar_wait(&empty[so], (uo - 1) & 1, abort, p.flags)) break;
             const uint32_t src = st0 + ss * TM_STAGE_X;
@@ -502,17 +533,21 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
         const int rt = (tid - TM_CONV_THREADS) % TM_RNG_THREADS;
         const int grp = (tid - TM_CONV_THREADS) / TM_RNG_THREADS;
         const int ncall = (p.K + 19) / 20;
-        for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS) {
-            const int64_t ch = blockIdx.x + t * gridDim.x;
-            const int so = (int)(t % S_op);
-            const uint32_t uo = (uint32_t)(t / S_op);
-            const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * p.kc;
+        const int nitems = p.kc * ncall;              // <= 64 * 4 = 2 * TM_RNG_THREADS
+        const int it0 = rt, it1 = rt + TM_RNG_THREADS;
+        const int rr0 = it0 % p.kc, cb0 = it0 / p.kc, rr1 = it1 % p.kc, cb1 = it1 / p.kc;
+        Ring ro(S_op, grp);
+        ChunkPos cp(blockIdx.x + (int64_t)grp * gridDim.x, (int64_t)TM_RNG_GROUPS * gridDim.x, p.nbc);
+        for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS, ro.step(TM_RNG_GROUPS), cp.step()) {
+            const int so = ro.slot;
+            const uint32_t uo = ro.use;
+            const int64_t a = cp.a, b0 = cp.bi * p.kc;
             const int64_t r0 = a * p.B + b0;
             const int len = (int)min((int64_t)p.kc, p.B - b0);
             if (t >= S_op && !mbar_wait(&empty[so], (uo - 1) & 1, abort, p.flags)) break;
             const uint32_t bt = op0 + so * op_bytes + 2 * MTILE_BYTES;
-            for (int item = rt; item < p.kc * ncall; item += TM_RNG_THREADS) {
-                const int rr = item % p.kc, cb = item / p.kc;
+            for (int item = it0; item < nitems; item += TM_RNG_THREADS) {
+                const int rr = item == it0 ? rr0 : rr1, cb = item == it0 ? cb0 : cb1;
                 uint64_t w[4] = {0, 0, 0, 0};
                 if (rr < len) rtr::omega_words(p.seed, p.mode, (uint64_t)(r0 + rr), (uint64_t)cb, w);
 #pragma unroll
@@ -528,12 +563,13 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     } else if (warp == TM_TMA_WARP) {
         // ================================================================ TMA producer
         if (lane == 0) {
-            for (int64_t t = 0; t < nloc; ++t) {
-                const int64_t ch = blockIdx.x + t * gridDim.x;
-                const int ss = (int)(t % S_st);
-                const uint32_t us = (uint32_t)(t / S_st);
+            Ring rs(S_st);
+            ChunkPos cp(blockIdx.x, gridDim.x, p.nbc);
+            for (int64_t t = 0; t < nloc; ++t, rs.step(1), cp.step()) {
+                const int ss = rs.slot;
+                const uint32_t us = rs.use;
                 if (t >= S_st && !mbar_wait(&stempty[ss], (us - 1) & 1, abort, p.flags)) break;
-                const int64_t a = ch / p.nbc, b0 = (ch % p.nbc) * p.kc;
+                const int64_t a = cp.a, b0 = cp.bi * p.kc;
                 // the full box is always counted: out-of-range rows (i >= I) and
                 // columns are zero-filled by the TMA unit without memory traffic
                 mbar_arrive_expect_tx(&stfull[ss], (uint32_t)(128 * 4 * p.kc));
@@ -544,9 +580,10 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     } else {
         // ================================================================ MMA issuer
         const uint32_t idesc = idesc_bf16_f32(128, p.N);
-        for (int64_t t = 0; t < nloc; ++t) {
-            const int so = (int)(t % S_op);
-            const uint32_t uo = (uint32_t)(t / S_op);
+        Ring ro(S_op);
+        for (int64_t t = 0; t < nloc; ++t, ro.step(1)) {
+            const int so = ro.slot;
+            const uint32_t uo = ro.use;
             if (!mbar_wait(&fullA[so], uo & 1, abort, p.flags)) break;
             if (!mbar_wait(&fullB[so], uo & 1, abort, p.flags)) break;
             tc_fence_after();
@@ -821,9 +858,13 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
     if (warp < TT_CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
-        auto load = [&](int64_t u, float4 (&v)[TT_PIECES]) {
-            const int64_t j = u / p.NKC;
-            const int c = (int)(u % p.NKC);
+        // units are loaded in order u = 0, 1, ...: (tile j, i-chunk c) advanced in step
+        int64_t lj = 0;
+        int lc = 0;
+        auto load = [&](float4 (&v)[TT_PIECES]) {
+            const int64_t j = lj;
+            const int c = lc;
+            if (++lc == p.NKC) { lc = 0; ++lj; }
             const int64_t a0 = (blockIdx.x + j * gridDim.x) * 128;
             const int rows = (int)min((int64_t)128, p.A - a0);
 #pragma unroll
@@ -844,8 +885,7 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
                 }
             }
         };
-        auto store = [&](int64_t u, const float4 (&v)[TT_PIECES]) {
-            const int s = (int)(u % S);
+        auto store = [&](int s, const float4 (&v)[TT_PIECES]) {
             const uint32_t hi = abase + s * a_stage, lo = hi + MTILE_BYTES;
 #pragma unroll
             for (int q = 0; q < TT_PIECES; ++q) {
@@ -860,43 +900,45 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
             }
         };
         float4 va[TT_PIECES], vb[TT_PIECES];
-        if (nunits > 0) load(0, va);
+        Ring rg(S);                                   // slot / use of the unit being stored
+        if (nunits > 0) load(va);
         for (int64_t u = 0; u < nunits; u += 2) {
             // unit u in va (loaded earlier); prefetch u + 1 into vb
-            if (u + 1 < nunits) load(u + 1, vb);
+            if (u + 1 < nunits) load(vb);
             {
-                const int s = (int)(u % S);
-                const uint32_t ph = (uint32_t)(u / S);
+                const int s = rg.slot;
+                const uint32_t ph = rg.use;
                 if (u >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
-                store(u, va);
+                store(s, va);
                 fence_proxy_async();
                 mbar_arrive(&fullA[s]);
+                rg.step(1);
             }
             if (u + 1 >= nunits) break;
-            if (u + 2 < nunits) load(u + 2, va);
+            if (u + 2 < nunits) load(va);
             {
-                const int64_t u1 = u + 1;
-                const int s = (int)(u1 % S);
-                const uint32_t ph = (uint32_t)(u1 / S);
-                if (u1 >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
-                store(u1, vb);
+                const int s = rg.slot;
+                const uint32_t ph = rg.use;
+                if (u + 1 >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
+                store(s, vb);
                 fence_proxy_async();
                 mbar_arrive(&fullA[s]);
+                rg.step(1);
             }
         }
     } else if (warp == TT_MMA_WARP) {
         // ================================================================ MMA issuer
         const uint32_t idesc = idesc_bf16_f32(128, p.N);
         bool ok = true;
+        Ring rg(S);
         for (int64_t j = 0; j < nloc && ok; ++j) {
             const int buf = (int)(j & 1);
             if (j >= 2 && !mbar_wait(&acce[buf], (uint32_t)(((j >> 1) - 1) & 1), abort, p.flags)) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(buf * p.N);
-            for (int c = 0; c < p.NKC; ++c) {
-                const int64_t u = j * p.NKC + c;
-                const int s = (int)(u % S);
-                if (!mbar_wait(&fullA[s], (uint32_t)((u / S) & 1), abort, p.flags)) { ok = false; break; }
+            for (int c = 0; c < p.NKC; ++c, rg.step(1)) {
+                const int s = rg.slot;
+                if (!mbar_wait(&fullA[s], rg.use & 1, abort, p.flags)) { ok = false; break; }
                 tc_fence_after();
                 if (lane == 0) {
                     const uint32_t ahi = abase + s * a_stage, alo = ahi + MTILE_BYTES;

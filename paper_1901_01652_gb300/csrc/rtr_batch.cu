@@ -27,6 +27,8 @@ struct rtr_batch {
     std::vector<double*> key_G;
     double* key_rse = nullptr;
     uint64_t graph_kernels = 0;        // kernel launches captured in `exec`
+    bool no_graph = false;
+    BatchAls* als = nullptr;           // grouped TR-ALS over all tensors (null: per-tensor ALS)
 };
 
 namespace {
@@ -44,35 +46,60 @@ void free_batch(rtr_batch* b) {
     if (b->start) cudaEventDestroy(b->start);
     if (b->origin) cudaStreamDestroy(b->origin);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->als) batch_als_destroy(b->als);
     delete b;
 }
 
 // Enqueue Algorithm 1 for every tensor on the worker streams, forked from and
-// joined back into `origin`.
-int enqueue(rtr_batch* b, const void* const* X, double* const* G, double* rse) {
-    const int N = b->N;
+// joined back into `origin`.  With the grouped TR-ALS, the sketches and
+// projection chains run per tensor on the workers, then one grouped ALS over
+// all tensors on `origin`, then back-projection and RSE per tensor again.
+int fork(rtr_batch* b) {
     for (int w = 0; w < b->nstreams; ++w) {
         RTR_CUDA(cudaEventRecord(b->fork[w], b->origin));
         RTR_CUDA(cudaStreamWaitEvent(b->workers[w], b->fork[w], 0));
     }
+    return RTR_OK;
+}
+int join(rtr_batch* b) {
+    for (int w = 0; w < b->nstreams; ++w) {
+        RTR_CUDA(cudaEventRecord(b->join[w], b->workers[w]));
+        RTR_CUDA(cudaStreamWaitEvent(b->origin, b->join[w], 0));
+    }
+    return RTR_OK;
+}
+
+int enqueue(rtr_batch* b, const void* const* X, double* const* G, double* rse) {
+    const int N = b->N;
+    int st = fork(b);
+    if (st) return st;
     for (int t = 0; t < b->count; ++t) {
         rtr_plan* p = b->plans[t];
         void* s = b->workers[t % b->nstreams];
         double* const* Y = b->Y.data() + (size_t)t * N;
         double* const* Q = b->Q.data() + (size_t)t * N;
         double* const* Z = b->Z.data() + (size_t)t * N;
-        int st = rtr_sketch(p, X[t], Y, s);
+        st = rtr_sketch(p, X[t], Y, s);
         if (!st) st = rtr_project(p, X[t], Y, Q, b->P[t], s);
-        if (!st) st = rtr_als(p, b->P[t], Z, 0, nullptr, s);
-        if (!st) st = rtr_backproject(p, Z, Q, G + (size_t)t * N, nullptr, s);
+        if (!st && !b->als) st = rtr_als(p, b->P[t], Z, 0, nullptr, s);
+        if (!st && !b->als) st = rtr_backproject(p, Z, Q, G + (size_t)t * N, nullptr, s);
+        if (!st && !b->als && rse) st = rtr_rse(p, b->P[t], Z, nullptr, rse + t, s);
+        if (st) return st;
+    }
+    if ((st = join(b))) return st;
+    if (!b->als) return RTR_OK;
+    if ((st = batch_als_run(b->als, nullptr, b->origin))) return st;
+    if ((st = fork(b))) return st;
+    for (int t = 0; t < b->count; ++t) {
+        rtr_plan* p = b->plans[t];
+        void* s = b->workers[t % b->nstreams];
+        double* const* Q = b->Q.data() + (size_t)t * N;
+        double* const* Z = b->Z.data() + (size_t)t * N;
+        st = rtr_backproject(p, Z, Q, G + (size_t)t * N, nullptr, s);
         if (!st && rse) st = rtr_rse(p, b->P[t], Z, nullptr, rse + t, s);
         if (st) return st;
     }
-    for (int w = 0; w < b->nstreams; ++w) {
-        RTR_CUDA(cudaEventRecord(b->join[w], b->workers[w]));
-        RTR_CUDA(cudaStreamWaitEvent(b->origin, b->join[w], 0));
-    }
-    return RTR_OK;
+    return join(b);
 }
 
 }  // namespace
@@ -90,6 +117,7 @@ int rtr_batch_create(rtr_batch** out, int count, int N, const int64_t* dims, con
     b->count = count;
     b->N = N;
     b->nstreams = std::min(nstreams, count);
+    b->no_graph = (params->flags & RTR_PARAM_NO_GRAPH) != 0;
     b->dims.assign(dims, dims + (size_t)count * N);
     const size_t esz = params->prec == RTR_FP64 ? 8 : 4;
 #define B_TRY(x) do { int s_ = (x); if (s_) { free_batch(b); return s_; } } while (0)
@@ -135,6 +163,24 @@ int rtr_batch_create(rtr_batch** out, int count, int N, const int64_t* dims, con
         B_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
         b->join.push_back(e2);
     }
+    {
+        // grouped TR-ALS when every tensor is within its limits (else per-tensor ALS)
+        std::vector<int64_t> Ke((size_t)count * N);
+        std::vector<uint64_t> seeds(count);
+        for (int t = 0; t < count; ++t) {
+            for (int n = 0; n < N; ++n) Ke[(size_t)t * N + n] = b->plans[t]->K[n];
+            seeds[t] = params->seed + (uint64_t)t;
+        }
+        int dev = 0;
+        B_CUDA(cudaGetDevice(&dev));
+        int sms = 0;
+        B_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int st = batch_als_create(&b->als, count, N, Ke.data(), R, params->prec == RTR_FP64,
+                                        params->sweeps, seeds.data(), b->plans[0]->tab64,
+                                        (const void* const*)b->P.data(), b->Z.data(), sms);
+        if (st == RTR_EUNSUPPORTED) b->als = nullptr;
+        else if (st) { free_batch(b); return st; }
+    }
 #undef B_TRY
 #undef B_CUDA
     *out = b;
@@ -169,6 +215,7 @@ int rtr_batch_run(rtr_batch* b, const void* const* X, double* const* G, double* 
     if (st) return st;
     RTR_CUDA(cudaEventRecord(b->start, b->origin));
     RTR_CUDA(cudaStreamWaitEvent(s, b->start, 0));
+    if (b->no_graph) return RTR_OK;
     // capture the same schedule for the next runs with these buffers
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     RTR_CUDA(cudaStreamSynchronize(b->origin));
@@ -186,6 +233,25 @@ int rtr_batch_run(rtr_batch* b, const void* const* X, double* const* G, double* 
     b->key_X.assign(X, X + b->count);
     b->key_G.assign(G, G + ng);
     b->key_rse = rse;
+    return RTR_OK;
+}
+
+int rtr_batch_flags(rtr_batch* b, int* flags) {
+    if (!b || !flags) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    int f = 0;
+    for (auto* p : b->plans) {
+        int pf = 0;
+        const int st = rtr_plan_flags(p, &pf);
+        if (st) return st;
+        f |= pf;
+    }
+    if (b->als) {
+        int af = 0;
+        const int st = batch_als_flags(b->als, &af);
+        if (st) return st;
+        f |= af;
+    }
+    *flags = f;
     return RTR_OK;
 }
 

@@ -108,6 +108,16 @@ int run_rse(rtr_plan* p, const void* P, const double* const* Z, const int* ranks
 int run_draw_omega(rtr_plan* p, int mode, int64_t row0, int64_t nrows, int K, double* out,
                    cudaStream_t s);
 
+// k_als_batch.cu: grouped TR-ALS over a batch of projected tensors of the
+// same order (default start, `sweeps` sweeps).  K, R: count*N effective
+// sizes and ranks; P, Z: per-tensor device buffers fixed at creation.
+struct BatchAls;
+int batch_als_create(BatchAls** out, int count, int N, const int64_t* K, const int* R, int is_f64, int sweeps,
+                     const uint64_t* seeds, const double* tab, const void* const* P, double* const* Z, int num_sms);
+void batch_als_destroy(BatchAls* b);
+int batch_als_run(BatchAls* b, double* err, cudaStream_t s);
+int batch_als_flags(BatchAls* b, int* flags);
+
 // k_trsvd.cu
 int run_trsvd(rtr_plan* p, const void* P, double tol, double* const* Z, int* ranks, cudaStream_t s);
 

@@ -18,6 +18,7 @@ RTR_OK, RTR_EINVAL, RTR_ENOMEM, RTR_ECUDA, RTR_ENONFINITE, RTR_ENOTCONV, RTR_ETI
 RTR_FP64, RTR_FP32, RTR_BF16 = 0, 1, 2
 PREC = {"fp64": RTR_FP64, "fp32": RTR_FP32, "bf16": RTR_BF16}
 FLAG_NONFINITE, FLAG_QR_FALLBACK, FLAG_GRAM_PINV, FLAG_TIMEOUT = 1, 2, 4, 8
+PARAM_NO_GRAPH = 1
 
 # every entry point of include/rtr.h
 ENTRY_POINTS = (
@@ -25,7 +26,7 @@ ENTRY_POINTS = (
     "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
     "rtr_sketch_mode_noalloc", "rtr_batch_create", "rtr_batch_destroy", "rtr_batch_run",
-    "rtr_batch_graph_kernels", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
+    "rtr_batch_graph_kernels", "rtr_batch_flags", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
     "rtr_mlp_forward", "rtr_mlp_grad", "rtr_mlp_adam", "rtr_mlp_status", "rtr_propose",
 )
 
@@ -83,6 +84,7 @@ def lib():
         "rtr_batch_destroy": (ctypes.c_int, [_VP]),
         "rtr_batch_run": (ctypes.c_int, [_VP, _VPP, _VPP, _VP, _VP]),
         "rtr_batch_graph_kernels": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+        "rtr_batch_flags": (ctypes.c_int, [_VP, _IP]),
         "rtr_mlp_param_count": (ctypes.c_size_t, []),
         "rtr_mlp_work_bytes": (ctypes.c_size_t, [ctypes.c_int]),
         "rtr_spectrum_features": (ctypes.c_int, [ctypes.c_int, _I64P, _IP, _VPP, _VP, _VP]),
@@ -311,6 +313,8 @@ class Batch:
 
 def rtr_batch_create(shapes, K, R, params, nstreams=8):
     """shapes, K, R: one sequence of N values per tensor."""
+    if len(shapes) == 0:
+        raise ValueError("a batch needs at least one tensor")
     N = len(shapes[0])
     if any(len(s) != N for s in list(shapes) + list(K) + list(R)) or not (len(shapes) == len(K) == len(R)):
         raise ValueError("every tensor needs N dims, K and R values")
@@ -333,6 +337,12 @@ def rtr_batch_run(batch, X, G, rse=None, stream=None):
     gs = _ptrs([g for gt in G for g in gt], torch.float64, "G")
     _dev(rse, torch.float64, "rse")
     _check(lib().rtr_batch_run(batch.handle, xs, gs, _ptr(rse), _stream(stream)))
+
+
+def rtr_batch_flags(batch):
+    f = ctypes.c_int(0)
+    _check(lib().rtr_batch_flags(batch.handle, ctypes.byref(f)))
+    return f.value
 
 
 def rtr_batch_graph_kernels(batch):

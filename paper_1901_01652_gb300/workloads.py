@@ -114,3 +114,18 @@ def to_pixels(x):
 def batch_ranks(dims, r):
     """Sketch sizes and TR ranks of one batch tensor: K_n = min(I_n, 2r), R_n = r."""
     return tuple(min(int(d), 2 * r) for d in dims), (r,) * len(dims)
+
+
+def proposer_shapes(count, seed=1906, snr=(30.0, 50.0), rlo=1, rhi=6):
+    """Training/evaluation tensors of the learned proposer: order 4 (modes
+    U{16..36}) or order 5 (modes U{10..18}) with equal probability, uniform TR
+    rank r ~ U{rlo..rhi}, SNR ~ U[snr] dB.  Returns (dims, r, snr_db, seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(count):
+        if rng.uniform() < 0.5:
+            dims = tuple(int(x) for x in rng.integers(16, 37, size=4))
+        else:
+            dims = tuple(int(x) for x in rng.integers(10, 19, size=5))
+        out.append((dims, int(rng.integers(rlo, rhi + 1)), float(rng.uniform(*snr)), seed + 7 * t + 1))
+    return out

@@ -82,3 +82,40 @@ def test_library_table_equals_oracle_table(L):
     assert np.max(np.abs(t64 - ref)) < 2e-15
     assert np.array_equal(rtr.rtr_gaussian_table("bf16"), omega.gaussian_table("bf16"))
     assert np.array_equal(rtr.rtr_gaussian_table("fp32"), omega.gaussian_table("fp32"))
+
+
+def test_propose_decoding_matches_oracle(L):
+    """rtr_propose is host code: its decoding of a network output equals the
+    oracle's (round half to even, clamps to [1, min(I_n, 64)] and [1, r_max])."""
+    from oracle import proposer as op
+    from paper_1901_01652_gb300 import rtr
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        out = rng.uniform(-0.2, 1.3, 10).astype(np.float32)
+        dims = tuple(int(x) for x in rng.integers(2, 120, size=int(rng.integers(3, 6))))
+        assert rtr.rtr_propose(out, dims) == op.decode(out.astype(np.float64), dims)
+    half = np.array([2.5 / 64, 0.5 / 16] * 5, dtype=np.float32)    # exact halves -> even
+    assert rtr.rtr_propose(half, (100, 100, 100)) == op.decode(half.astype(np.float64), (100, 100, 100))
+    with pytest.raises(rtr.RtrError):
+        rtr.rtr_propose(half, (10,) * 6)                            # more than 5 modes
+
+
+def test_proposer_sizes(L):
+    from oracle import proposer as op
+    from paper_1901_01652_gb300 import rtr
+    assert rtr.rtr_mlp_param_count() == op.param_count()
+    assert rtr.rtr_mlp_work_bytes(0) == 0
+    assert rtr.rtr_mlp_work_bytes(100) >= 100 * (6 * 128 + 20) * 4
+
+
+def test_batch_create_rejects_bad_arguments_on_host(L):
+    from paper_1901_01652_gb300 import rtr
+    p = rtr.make_params("fp32", 1, 2)
+    with pytest.raises(ValueError):
+        rtr.rtr_batch_create([], [], [], p)
+    with pytest.raises(rtr.RtrError) as e:
+        rtr.rtr_batch_create([(8, 8, 8)], [(4, 4, 4)], [(2, 2, 2)], p, nstreams=65)
+    assert e.value.status == rtr.RTR_EINVAL
+    p.chain_order[1] = 0
+    with pytest.raises(rtr.RtrError):
+        rtr.rtr_batch_create([(8, 8, 8)], [(4, 4, 4)], [(2, 2, 2)], p)

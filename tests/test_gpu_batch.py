@@ -98,6 +98,19 @@ def test_batch_bf16_graph_replay_and_new_data():
             assert abs(rse[t] - refs[t][1]) <= 1e-3 * max(1e-3, refs[t][1]) + 1e-6, t
 
 
+def test_batch_bf16_large_ranks_vs_oracle():
+    """The batched workload's recipe at ranks 8..12 (Gram matrices up to
+    144 x 144, K_n R_n R_{n+1} up to 3456): every tensor within 1e-3."""
+    shapes, Xs, Ks, Rs = small_batch(4, 20, 30, 8, 12, 90)
+    b, outs = run_batch(shapes, Xs, Ks, Rs, "bf16", 91, 5, nstreams=2)
+    assert rtr.rtr_batch_flags(b) & ~rtr.FLAG_GRAM_PINV == 0
+    refs = oracle_batch(Xs, Ks, Rs, "bf16", 91, 5)
+    cores, rse = outs[0]
+    for t in range(len(shapes)):
+        assert rel(ot.tr_full(cores[t]), refs[t][0]) <= 1e-3, (t, shapes[t], Rs[t])
+        assert abs(rse[t] - refs[t][1]) <= 1e-3 * refs[t][1] + 1e-6, t
+
+
 def test_batch_argument_errors():
     params = rtr.make_params("fp32", 1, 2)
     with pytest.raises(ValueError):
