@@ -13,6 +13,8 @@ Application to Large-scale Data Reconstruction", arXiv:1901.01652):
 * ``philox``  - Philox4x64-10 counter-based generator (Salmon et al., SC'11),
                 the source of the Gaussian test matrices (Algorithm 1, step 4).
 * ``omega``   - the Gaussian quantile table and the test matrices Omega_n.
+* ``mxfp8``   - block-scaled float8 (e4m3, one power-of-two scale per 32
+                values) copy of X read by the FP8 form of the sketch.
 * ``tensor``  - unfoldings, mode-n products, TR format (Eq. 1, Eq. 2).
 * ``rtrd``    - Algorithm 1 (sketch, QR, projection, back-projection), the
                 TR-ALS and TR-SVD decomposers it calls, RSE (Section 4).

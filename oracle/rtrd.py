@@ -7,6 +7,7 @@ in the docstrings.
 import numpy as np
 import scipy.linalg
 
+from . import mxfp8 as _mxfp8
 from . import omega as _omega
 from .tensor import (core_matrix, fro, mode_product, mode_view, subchain_matrix,
                      tr_full, tr_unfold, unfold)
@@ -30,7 +31,9 @@ def projected(dims, K):
 def sketch(X, K, seed, prec="fp64"):
     """Algorithm 1, steps 4-5: Y_n = X_(n) M with M the Gaussian test matrix
     Omega_n (see ``oracle.omega``).  Returns [Y_n] (None for modes that are
-    not projected)."""
+    not projected).  With prec="fp8" the sketch of mode n reads the
+    block-scaled float8 copy of X defined in ``oracle.mxfp8`` (the rest of
+    the algorithm still uses X itself)."""
     Y = []
     for n, k in enumerate(K):
         A, I, B = mode_view(X.shape, n)
@@ -38,7 +41,8 @@ def sketch(X, K, seed, prec="fp64"):
             Y.append(None)
             continue
         Om = _omega.omega(seed, n, A * B, k, prec)
-        Y.append(unfold(X, n) @ Om)
+        Xs = _mxfp8.quantize_for_mode(X, n) if prec == "fp8" else X
+        Y.append(unfold(Xs, n) @ Om)
     return Y
 
 
