@@ -9,7 +9,7 @@ and the RSE identity.  The input is synthetic, built on the GPU from seeded
 cores; it is larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--prec bf16|fp32] [--size S] [--no-cpu-baseline]
+                  [--prec bf16|fp32|fp8] [--size S] [--no-cpu-baseline]
 
 Multi-GPU: replicas only (each rank decomposes its own tensor, no collective
 on the data path); value = all ranks' bytes / max-over-ranks time.
@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--prec", default=None, choices=["bf16", "fp32", "fp8"],
+                    help="sketch/chain arithmetic (default: bf16 for c2, the workload's own for c1/c3)")
     ap.add_argument("--size", type=int, default=200, help="mode length (200 = the named workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -262,7 +263,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
+        "dtype": {"bf16": "bf16", "fp32": "f32", "fp8": "fp8-e4m3 sketch, bf16 chain"}[args.prec], "data": "synthetic",
         "config": {"workload": WORKLOAD if S == 200 else f"rTR-ALS order-4 {S}^4 fp32 (reduced)",
                    "dims": list(dims), "K": list(K), "R": list(R), "sweeps": sweeps, "snr_db": snr,
                    "prec": args.prec, "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
@@ -523,8 +524,8 @@ SINGLE = {
                dims=(60, 60, 60, 60), K=(15,) * 4, R=(5,) * 4, prec="fp64", method="als", sweeps=20,
                eps=None, seed=1902, sample=(30, 30, 30, 30)),
     "c3": dict(workload="rTR-SVD hyperspectral-shaped 1024x1024x256 fp32 (1.07 GB), 20 abundance maps x 20 "
-                        "spectra + 1% noise, K=(60,60,30), eps=1e-2, BF16 sketch",
-               dims=(1024, 1024, 256), K=(60, 60, 30), R=(16, 16, 16), prec="bf16", method="svd", sweeps=1,
+                        "spectra + 1% noise, K=(60,60,30), eps=1e-2, block-scaled FP8 sketch",
+               dims=(1024, 1024, 256), K=(60, 60, 30), R=(16, 16, 16), prec="fp8", method="svd", sweeps=1,
                eps=1e-2, seed=1904, sample=(256, 256, 64)),
 }
 
@@ -564,13 +565,13 @@ def single_input(name, dims, seed, device, host=False):
     return X.float().contiguous()
 
 
-def single_step(eng, X, spec, stream):
+def single_step(eng, X, spec, stream, ranks=None):
     eng.sketch(X, stream)
     eng.project(X, stream)
     if spec["method"] == "als":
         eng.als(None, stream)
     else:
-        eng.svd(spec["eps"], None, stream)
+        eng.svd(spec["eps"], ranks, stream)
     eng.backproject(stream)
     eng.compute_rse(stream)
 
@@ -579,7 +580,9 @@ def run_single(args):
     import torch
     from paper_1901_01652_gb300 import build, rtr
     from paper_1901_01652_gb300.api import RTRD, decompose
-    spec = SINGLE[args.workload]
+    spec = dict(SINGLE[args.workload])
+    if args.prec is not None and spec["prec"] != "fp64":
+        spec["prec"] = args.prec
     local = int(os.environ.get("LOCAL_RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -620,7 +623,8 @@ def run_single(args):
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if spec["prec"] == "fp64" else "bf16",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "fp8": "fp8-e4m3 sketch, bf16 chain"}[spec["prec"]],
         "data": "synthetic",
         "config": {"workload": spec["workload"], "dims": list(spec["dims"]), "K": list(spec["K"]),
                    "prec": spec["prec"], "method": spec["method"], "l2": "inputs larger than L2 (no flush)"
@@ -633,6 +637,29 @@ def run_single(args):
                      "traffic": None, "kernel": f"sketch_{spec['prec']}_{args.workload} (mean per mode)",
                      "sketch_ms_per_mode": round(sk_ms, 4)},
     }
+    if not args.no_plain and spec["prec"] not in ("fp64", "fp32"):
+        # plain FP32 arm on the same tensor, and how far the two reconstructions
+        # are apart; TR-SVD ranks forced to the mixed arm's choice (equal ranks)
+        plain = RTRD(spec["dims"], spec["K"], spec["R"], "fp32", spec["seed"], spec["sweeps"],
+                     spec["eps"] or 1e-2, device=device)
+        fr = list(eng.ranks) if spec["method"] == "svd" else None
+        single_step(plain, X, spec, stream, fr)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        psteps = max(1, args.steps // 2)
+        p0.record(stream)
+        for _ in range(psteps):
+            single_step(plain, X, spec, stream, fr)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / psteps
+        Xm = eng.reconstruct("fp32")
+        Xp = plain.reconstruct("fp32")
+        out["plain_fp32"] = {"value": round(world * xbytes / (pms * 1e-3) / 1e9, 3), "ms_per_step": round(pms, 4),
+                             "rse": float(plain.rse.cpu()[0]), "ranks": list(plain.ranks)}
+        out["mixed_vs_plain_rel_diff"] = float(torch.linalg.vector_norm(Xm - Xp, dtype=torch.float64) /
+                                               torch.linalg.vector_norm(Xp, dtype=torch.float64))
+        del Xm, Xp, plain
     if not args.no_e2e:
         Xh = X.cpu().pin_memory()
         decompose(Xh, spec["K"], spec["R"], spec["method"], spec["prec"], spec["seed"], spec["sweeps"],
@@ -676,4 +703,5 @@ if __name__ == "__main__":
     elif a.workload in SINGLE:
         run_single(a)
     else:
+        a.prec = a.prec or "bf16"
         run_ours(a)

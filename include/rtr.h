@@ -49,6 +49,17 @@ extern "C" {
 #define RTR_FP64  0   /* X float64; every step float64                            */
 #define RTR_FP32  1   /* X float32; SIMT float32 sketch / chain, float64 QR & solves */
 #define RTR_BF16  2   /* X float32; tcgen05 BF16 (hi+lo split) sketch / chain      */
+#define RTR_FP8   3   /* X float32; the sketch reads a block-scaled float8 copy of X:
+                         e4m3 values with one power-of-two scale per block of 32
+                         (blocks run along b of each (a, i) fibre of the (A, I_n, B)
+                         mode view, along a when B = 1; scale exponent
+                         max(floor(log2 amax) - 8, -120); round to nearest even,
+                         saturate at 448) against the e4m3-rounded quantile table.
+                         The dequantised values are exact in bfloat16, so one BF16
+                         tcgen05 MMA per step forms the same products with FP32
+                         accumulation.  Quantisation happens in the kernel's
+                         registers (X stays float32 in memory).  Everything after
+                         the sketch runs as for RTR_BF16. */
 
 /* rtr_params.flags bits */
 #define RTR_PARAM_NO_GRAPH     1   /* rtr_batch_run: always run eagerly, never capture a graph */
@@ -62,7 +73,7 @@ extern "C" {
 typedef struct rtr_plan rtr_plan;
 
 typedef struct {
-    int      prec;            /* RTR_FP64 / RTR_FP32 / RTR_BF16 */
+    int      prec;            /* RTR_FP64 / RTR_FP32 / RTR_BF16 / RTR_FP8 */
     uint64_t seed;            /* seed of the Gaussian test matrices Omega_n */
     int      sweeps;          /* TR-ALS sweeps (each updates cores 1..N once) */
     double   tol;             /* TR-SVD relative tolerance epsilon */
@@ -106,9 +117,12 @@ int rtr_plan_flags(rtr_plan* plan, int* flags);
  * stored: entry (r, k) is generated in the kernel from Philox4x64-10 with key
  * (seed, n) and counter (r, k/20, 0, 0) mapped through the 4096-level Gaussian
  * quantile table (float64 values for RTR_FP64, bfloat16-rounded values for
- * RTR_FP32 and RTR_BF16); r is the row-major index of the other modes.
+ * RTR_FP32 and RTR_BF16, e4m3-rounded values for RTR_FP8); r is the row-major
+ * index of the other modes.  RTR_FP8 plans sketch the block-scaled float8 copy
+ * of X described at RTR_FP8; they need a 16-byte aligned X and, per projected
+ * mode, B % 4 == 0 (B > 1) or I_n % 4 == 0 (B = 1), else RTR_EUNSUPPORTED.
  * Y[n] may be NULL for modes that are not projected.  Also records ||X||_F^2
- * in the plan for rtr_rse.
+ * (of X itself, not of its float8 copy) in the plan for rtr_rse.
  */
 int rtr_sketch(rtr_plan* plan, const void* X, double* const* Y, void* stream);
 

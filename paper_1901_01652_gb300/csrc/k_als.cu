@@ -683,7 +683,7 @@ __global__ void rse_final_kernel(const double* __restrict__ part, int nparts, co
 
 __global__ void draw_omega_kernel(double* __restrict__ out, int64_t row0, int64_t nrows, int K, uint64_t seed,
                                   int mode, const double* __restrict__ tab64, const float* __restrict__ tab32,
-                                  int use64) {
+                                  const uint16_t* __restrict__ tab16, int use64) {
     const int ncalls = (K + 19) / 20;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nrows * ncalls;
          w += (int64_t)gridDim.x * blockDim.x) {
@@ -695,7 +695,9 @@ __global__ void draw_omega_kernel(double* __restrict__ out, int64_t row0, int64_
             const int k = cb * 20 + t;
             if (k < K) {
                 const int j = rtr::omega_field(wd, t);
-                out[rr * K + k] = use64 ? tab64[j] : (double)tab32[j];
+                out[rr * K + k] = use64 ? tab64[j]
+                                  : tab16 ? (double)__uint_as_float((uint32_t)tab16[j] << 16)   // bfloat16 bits
+                                          : (double)tab32[j];
             }
         }
     }
@@ -1015,7 +1017,9 @@ int run_rse(rtr_plan* p, const void* P, const double* const* Z, const int* ranks
 int run_draw_omega(rtr_plan* p, int mode, int64_t row0, int64_t nrows, int K, double* out, cudaStream_t s) {
     const int ncalls = (K + 19) / 20;
     draw_omega_kernel<<<grid_for(nrows * ncalls), 256, 0, s>>>(out, row0, nrows, K, p->params.seed, mode, p->tab64,
-                                                               p->tab32, p->params.prec == RTR_FP64);
+                                                               p->tab32,
+                                                               p->params.prec == RTR_FP8 ? p->tab_e4m3 : nullptr,
+                                                               p->params.prec == RTR_FP64);
     RTR_LAUNCH_CHECK("draw_omega_kernel");
     return RTR_OK;
 }

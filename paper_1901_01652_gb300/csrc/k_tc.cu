@@ -68,6 +68,7 @@ struct SketchTCArgs {
     uint64_t seed;
     int mode;
     int vec;                      // 1: 16-byte vector loads are legal
+    int fp8;                      // 1: block-scaled float8 values, one MMA (last mode, vec only)
     const uint16_t* tab;          // bfloat16 table (global)
     double* partial;              // [gridDim.x][I][K]
     double* normp;                // [gridDim.y * gridDim.x] or null
@@ -211,10 +212,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
 #pragma unroll
                             for (int v = 0; v < 4; ++v) {
                                 const int row = 4 * u4 + v;
-                                uint32_t h, l;
-                                split2(a0v[v], a1v[v], h, l);
                                 csum += a0v[v] * a0v[v] + a1v[v] * a1v[v];
                                 const uint32_t off = (uint32_t)(row >> 7) * MTILE_BYTES + sw128_off(row & 127, 2 * q);
+                                if (p.fp8) {
+                                    // scale block = 32 consecutive r = a of this row: lanes
+                                    // q = 0..15 hold r 0..31 of the chunk, q = 16..31 the rest
+                                    // (the item test above is uniform per warp)
+                                    const float m = group_max(fmaxf(fabsf(a0v[v]), fabsf(a1v[v])), 16);
+                                    st_shared_u32(hi_base + off, mx_pair(a0v[v], a1v[v], mx_scale(m)));
+                                    continue;
+                                }
+                                uint32_t h, l;
+                                split2(a0v[v], a1v[v], h, l);
                                 st_shared_u32(hi_base + off, h);
                                 st_shared_u32(lo_base + off, l);
                             }
@@ -293,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
                     for (int j = 0; j < KC / 16; ++j) {
                         const uint64_t bd = sdesc_sw128(bb + 32u * j);
                         mma_bf16(d, sdesc_sw128(ahi + m * MTILE_BYTES + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                        mma_bf16(d, sdesc_sw128(alo + m * MTILE_BYTES + 32u * j), bd, idesc, 1u);
+                        if (!p.fp8) mma_bf16(d, sdesc_sw128(alo + m * MTILE_BYTES + 32u * j), bd, idesc, 1u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -392,7 +401,9 @@ constexpr uint32_t TM_STAGE_X = 128 * 64 * 4;     // fp32 staging tile
 struct SketchTmaArgs {
     int64_t A, B;
     int I, K, N, S_st, S_op;
-    int kc;                       // chunk width along b: a multiple of 8 dividing B (or 64)
+    int kc;                       // chunk width along b: a multiple of 8 dividing B (or 64);
+                                  // FP8: 64 or 32 (whole 32-value scale blocks)
+    int fp8;                      // 1: block-scaled float8 values, one MMA (no lo part)
     int64_t nchunks, nbc;
     uint64_t seed;
     int mode;
@@ -470,11 +481,19 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
             const uint32_t hi = op0 + so * op_bytes, lo = hi + MTILE_BYTES;
             float csum = 0.f;
             auto piece = [&](const float4 v, int row, int c4) {
+                if (row < rows_valid) csum += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                const uint32_t off = sw128_off(row, 4 * c4);
+                if (p.fp8) {
+                    // a 32-value scale block is 8 consecutive pieces of one row,
+                    // held by 8 consecutive lanes (kc = 32 or 64)
+                    const float m = group_max(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))), 8);
+                    const MxScale sc = mx_scale(m);
+                    st_shared_v2(hi + off, mx_pair(v.x, v.y, sc), mx_pair(v.z, v.w, sc));
+                    return;
+                }
                 uint32_t h0, l0, h1, l1;
                 split2(v.x, v.y, h0, l0);
                 split2(v.z, v.w, h1, l1);
-                if (row < rows_valid) csum += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
-                const uint32_t off = sw128_off(row, 4 * c4);
                 st_shared_v2(hi + off, h0, h1);
                 st_shared_v2(lo + off, l0, l1);
             };
@@ -593,7 +612,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                 for (int j = 0; j < ksteps; ++j) {
                     const uint64_t bd = sdesc_sw128(bb + 32u * j);
                     mma_bf16(tmem, sdesc_sw128(ahi + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                    mma_bf16(tmem, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
+                    if (!p.fp8) mma_bf16(tmem, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
                 }
                 mma_commit(&empty[so]);
             }
@@ -678,17 +697,22 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     SketchTmaArgs a{};
     a.A = A; a.B = B; a.I = (int)I; a.K = K;
     a.N = (K <= 32) ? 32 : 64;
+    a.fp8 = p->params.prec == RTR_FP8 ? 1 : 0;
     // chunk width: 64, or the largest multiple of 8 up to 64 that divides B
-    // (no ragged tail chunk, e.g. 40 for B = 200)
+    // (no ragged tail chunk, e.g. 40 for B = 200).  FP8 chunks hold whole
+    // 32-value scale blocks: 64 or 32, the ragged tail of each b-run
+    // zero-filled by the TMA unit.
     a.kc = 64;
-    if (B % 64 != 0) {
+    if (a.fp8) {
+        if (B % 64 != 0) a.kc = 32;
+    } else if (B % 64 != 0) {
         for (int w = 56; w >= 8; w -= 8)
             if (B % w == 0) { a.kc = w; break; }
     }
     a.nbc = rtr_ceil_div(B, a.kc);
     a.nchunks = A * a.nbc;
     a.seed = p->params.seed; a.mode = n;
-    a.tab = p->tab_bf16; a.flags = p->flags;
+    a.tab = a.fp8 ? p->tab_e4m3 : p->tab_bf16; a.flags = p->flags;
     const size_t fixed = 8192 + 64 * 8 + 2048;
     const size_t op = 2 * (size_t)MTILE_BYTES + (size_t)a.N * 128;
     a.S_st = 3;
@@ -732,12 +756,19 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
         rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
         const int K = p->K[n];
         const bool aligned16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+        const bool fp8 = p->params.prec == RTR_FP8;
         if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder()) {
             int st = launch_sketch_tma(p, X, A, I, B, n, Y[n], norm_done ? nullptr : p->scal + 0, s);
             if (st) return st;
             norm_done = true;
             continue;
         }
+        // the FP8 form exists in the TMA kernel (B > 1) and in the vectorised
+        // last-mode path of sketch_tc_kernel only
+        if (fp8 && (B > 1 || !aligned16 || I % 4 != 0))
+            return rtr_set_error(RTR_EUNSUPPORTED,
+                                 "FP8 sketch of mode %d needs a 16-byte aligned X and %s", n,
+                                 B > 1 ? "B % 4 == 0 (TMA path)" : "I_n % 4 == 0");
         int MT, N, S;
         size_t smem;
         if (!sketch_geometry(I, K, &MT, &N, &S, &smem))
@@ -749,7 +780,8 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
         a.seed = p->params.seed; a.mode = n;
         const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
         a.vec = aligned && ((B > 1) ? (B % 4 == 0) : (I % 4 == 0)) ? 1 : 0;
-        a.tab = p->tab_bf16;
+        a.fp8 = fp8 ? 1 : 0;
+        a.tab = fp8 ? p->tab_e4m3 : p->tab_bf16;
         a.flags = p->flags;
         const int gy = (int)rtr_ceil_div(I, a.rows_cta);
         int64_t gx = std::max<int64_t>(1, p->num_sms / gy);

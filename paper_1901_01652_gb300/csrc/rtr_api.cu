@@ -62,6 +62,21 @@ uint16_t bf16_bits(double x) {
     std::memcpy(&u, &f, 4);
     return (uint16_t)(u >> 16);
 }
+// round a double to the nearest float8 e4m3 value: 4 significant bits, ties
+// to even, spacing 2^-9 below the smallest normal 2^-6, saturated at 448
+double e4m3_value(double x) {
+    const double a = std::fabs(x);
+    double q;
+    if (a < 0.015625) {
+        q = std::ldexp(std::nearbyint(std::ldexp(a, 9)), -9);
+    } else {
+        int e;
+        const double m = std::frexp(a, &e);               // m in [0.5, 1)
+        q = std::ldexp(std::nearbyint(std::ldexp(m, 4)), e - 4);
+    }
+    q = std::min(q, 448.0);
+    return std::copysign(q, x);
+}
 float bf16_value(uint16_t b) {
     const uint32_t u = (uint32_t)b << 16;
     float f;
@@ -97,7 +112,7 @@ int choose_order(rtr_plan* p) {
 
 void free_plan(rtr_plan* p) {
     if (!p) return;
-    cudaFree(p->tab64); cudaFree(p->tab32); cudaFree(p->tab_bf16);
+    cudaFree(p->tab64); cudaFree(p->tab32); cudaFree(p->tab_bf16); cudaFree(p->tab_e4m3);
     cudaFree(p->partial); cudaFree(p->normx_part); cudaFree(p->scal);
     cudaFree(p->chain[0]); cudaFree(p->chain[1]);
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
@@ -157,6 +172,7 @@ int rtr_gaussian_table(int prec, double* out) {
     for (int j = 0; j < 4096; ++j) {
         if (prec == RTR_FP64) out[j] = t[j];
         else if (prec == RTR_FP32 || prec == RTR_BF16) out[j] = (double)bf16_value(bf16_bits(t[j]));
+        else if (prec == RTR_FP8) out[j] = e4m3_value(t[j]);
         else return rtr_set_error(RTR_EINVAL, "unknown precision %d", prec);
     }
     return RTR_OK;
@@ -167,7 +183,8 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     if (!plan || !dims || !K || !R || !params) return rtr_set_error(RTR_EINVAL, "NULL argument");
     *plan = nullptr;
     if (N < 3 || N > RTR_MAXN) return rtr_set_error(RTR_EINVAL, "order N=%d outside [3, 8]", N);
-    if (params->prec != RTR_FP64 && params->prec != RTR_FP32 && params->prec != RTR_BF16)
+    if (params->prec != RTR_FP64 && params->prec != RTR_FP32 && params->prec != RTR_BF16 &&
+        params->prec != RTR_FP8)
         return rtr_set_error(RTR_EINVAL, "unknown precision %d", params->prec);
     if (params->sweeps < 0) return rtr_set_error(RTR_EINVAL, "sweeps < 0");
     rtr_plan* p = new (std::nothrow) rtr_plan();
@@ -243,8 +260,12 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     double t64[4096];
     gaussian_table64(t64);
     float t32[4096];
-    uint16_t tb[4096];
-    for (int j = 0; j < 4096; ++j) { tb[j] = bf16_bits(t64[j]); t32[j] = bf16_value(tb[j]); }
+    uint16_t tb[4096], t8[4096];
+    for (int j = 0; j < 4096; ++j) {
+        tb[j] = bf16_bits(t64[j]);
+        t32[j] = bf16_value(tb[j]);
+        t8[j] = bf16_bits(e4m3_value(t64[j]));     // exact: 4 significant bits
+    }
 #define RTR_TRY(x) do { int s_ = (x); if (s_) { free_plan(p); return s_; } } while (0)
 #define RTR_TRYC(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { free_plan(p); return rtr_cuda_check(e_, #x); } } while (0)
     RTR_TRY(dalloc(&p->tab64, 4096));
@@ -253,6 +274,10 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     RTR_TRYC(cudaMemcpy(p->tab64, t64, sizeof(t64), cudaMemcpyHostToDevice));
     RTR_TRYC(cudaMemcpy(p->tab32, t32, sizeof(t32), cudaMemcpyHostToDevice));
     RTR_TRYC(cudaMemcpy(p->tab_bf16, tb, sizeof(tb), cudaMemcpyHostToDevice));
+    if (params->prec == RTR_FP8) {
+        RTR_TRY(dalloc(&p->tab_e4m3, 4096));
+        RTR_TRYC(cudaMemcpy(p->tab_e4m3, t8, sizeof(t8), cudaMemcpyHostToDevice));
+    }
     RTR_TRY(dalloc(&p->partial, part)); p->partial_elems = part;
     RTR_TRY(dalloc(&p->normx_part, normp)); p->normx_part_elems = normp;
     RTR_TRY(dalloc(&p->scal, 64));
@@ -326,7 +351,7 @@ int rtr_sketch(rtr_plan* p, const void* X, double* const* Y, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     for (int n = 0; n < p->N; ++n)
         if (p->proj[n] && !Y[n]) return rtr_set_error(RTR_EINVAL, "Y[%d] is NULL", n);
-    if (p->params.prec == RTR_BF16) return launch_sketch_tc(p, (const float*)X, Y, s);
+    if (p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8) return launch_sketch_tc(p, (const float*)X, Y, s);
     const int f64 = p->params.prec == RTR_FP64;
     bool norm_done = false;
     for (int n = 0; n < p->N; ++n) {
@@ -370,7 +395,7 @@ int rtr_project(rtr_plan* p, const void* X, const double* const* Y, double* cons
         int64_t A, I, B;
         rtr_mode_view(p->N, cd, n, &A, &I, &B);
         void* out = (step == nsteps - 1) ? P : p->chain[step & 1];
-        if (p->params.prec == RTR_BF16 && step == 0)
+        if ((p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8) && step == 0)
             st = launch_ttm_tc(p, (const float*)cur, A, I, B, Q[n], p->K[n], (float*)out, s);
         else
             st = launch_ttm(p, f64, cur, A, I, B, Q[n], p->K[n], out, s);

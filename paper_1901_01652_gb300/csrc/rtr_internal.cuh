@@ -28,6 +28,7 @@ struct rtr_plan {
     double* tab64 = nullptr;     // float64 quantiles
     float* tab32 = nullptr;      // bfloat16-rounded quantiles as float
     uint16_t* tab_bf16 = nullptr;// bfloat16 bit patterns
+    uint16_t* tab_e4m3 = nullptr;// e4m3-rounded quantiles as bfloat16 bit patterns (exact)
 
     // workspace
     double* partial = nullptr;   size_t partial_elems = 0;    // split-K partials

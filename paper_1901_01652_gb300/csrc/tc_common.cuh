@@ -2,6 +2,7 @@
 // mbarriers with bounded waits, tcgen05 MMA / TMEM / shared-memory descriptors.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include "rtr_internal.cuh"
 
 namespace rtr {
@@ -171,6 +172,37 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
     __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
     hi = *reinterpret_cast<uint32_t*>(&h);
     lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
+// ---- block-scaled float8 (e4m3) rounding -------------------------------------
+// A block of values with maximum magnitude amax gets the power-of-two scale
+// 2^e, e = max(floor(log2 amax) - 8, -120) (8: exponent of the largest power
+// of two in e4m3; -120 keeps every dequantised value exact in bfloat16).
+struct MxScale {
+    float inv, s;    // 2^-e, 2^e
+};
+__device__ __forceinline__ MxScale mx_scale(float amax) {
+    const int E = (__float_as_int(amax) >> 23) & 0xFF;      // biased exponent (0: zero or subnormal)
+    const int e = max(E - 135, -120);                       // E - 127 - 8
+    return {__int_as_float((127 - e) << 23), __int_as_float((127 + e) << 23)};
+}
+
+// Dequantised float8 values of a pair sharing scale m: round x * 2^-e to the
+// nearest e4m3 value (ties to even, saturated at 448), multiply back by 2^e,
+// and pack the two (exact) results as a bfloat16x2 word, x0 in the low half.
+__device__ __forceinline__ uint32_t mx_pair(float x0, float x1, const MxScale& m) {
+    const __nv_fp8x2_storage_t q =
+        __nv_cvt_float2_to_fp8x2(make_float2(x0 * m.inv, x1 * m.inv), __NV_SATFINITE, __NV_E4M3);
+    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
+    const float2 f = __half22float2(__half2(hr));
+    __nv_bfloat162 b = __floats2bfloat162_rn(f.x * m.s, f.y * m.s);
+    return *reinterpret_cast<uint32_t*>(&b);
+}
+
+// maximum over aligned groups of `width` lanes (width a power of two <= 32)
+__device__ __forceinline__ float group_max(float v, int width) {
+    for (int o = 1; o < width; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {

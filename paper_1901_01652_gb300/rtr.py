@@ -15,8 +15,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librtr.so")
 
 RTR_OK, RTR_EINVAL, RTR_ENOMEM, RTR_ECUDA, RTR_ENONFINITE, RTR_ENOTCONV, RTR_ETIMEOUT, RTR_EUNSUPPORTED = range(8)
-RTR_FP64, RTR_FP32, RTR_BF16 = 0, 1, 2
-PREC = {"fp64": RTR_FP64, "fp32": RTR_FP32, "bf16": RTR_BF16}
+RTR_FP64, RTR_FP32, RTR_BF16, RTR_FP8 = 0, 1, 2, 3
+PREC = {"fp64": RTR_FP64, "fp32": RTR_FP32, "bf16": RTR_BF16, "fp8": RTR_FP8}
 FLAG_NONFINITE, FLAG_QR_FALLBACK, FLAG_GRAM_PINV, FLAG_TIMEOUT = 1, 2, 4, 8
 PARAM_NO_GRAPH = 1
 

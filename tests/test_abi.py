@@ -82,6 +82,9 @@ def test_library_table_equals_oracle_table(L):
     assert np.max(np.abs(t64 - ref)) < 2e-15
     assert np.array_equal(rtr.rtr_gaussian_table("bf16"), omega.gaussian_table("bf16"))
     assert np.array_equal(rtr.rtr_gaussian_table("fp32"), omega.gaussian_table("fp32"))
+    # e4m3 rounding (subnormal grid below 2^-6, ties to even) written
+    # independently on both sides
+    assert np.array_equal(rtr.rtr_gaussian_table("fp8"), omega.gaussian_table("fp8"))
 
 
 def test_propose_decoding_matches_oracle(L):
