@@ -66,10 +66,10 @@ __device__ __forceinline__ void wtile_accum(T (&acc)[TILE_IP][4], const WTile& w
     }
 }
 
-// out[i * C + c] = acc (float64), for the valid (i, c) of this thread
-template <typename T>
+// out[i * C + c] = acc (converted to O), for the valid (i, c) of this thread
+template <typename T, typename O>
 __device__ __forceinline__ void wtile_store(const T (&acc)[TILE_IP][4], const WTile& w, int Kn, int C,
-                                            double* __restrict__ out) {
+                                            O* __restrict__ out) {
     if (!w.active) return;
 #pragma unroll
     for (int k = 0; k < TILE_IP; ++k) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ void wtile_store(const T (&acc)[TILE_IP][4], const WT
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int c = w.c0 + j;
-                if (c < C) out[(int64_t)i * C + c] = (double)acc[k][j];
+                if (c < C) out[(int64_t)i * C + c] = (O)acc[k][j];
             }
         }
     }

@@ -63,14 +63,22 @@ __device__ inline void warp_chol_solve(const double* L, int n, int ld, double* w
     }
 }
 
+// Sum of v over the block, returned to every thread (fixed order: warp
+// butterflies, then one butterfly over the warp sums).  Only warp 0 adds the
+// warp sums: a float64 add in every thread would load GB300's narrow FP64 pipe.
 __device__ inline double block_sum(double v, double* red /* >= 32 doubles */) {
     v = warp_sum(v);
-    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
+    if (lane == 0) red[w] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int i = 0; i < nw; ++i) s += red[i];
+    if (w == 0) {
+        double s = lane < nw ? red[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    const double s = red[0];
     __syncthreads();
     return s;
 }

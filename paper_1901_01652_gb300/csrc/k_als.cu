@@ -16,7 +16,6 @@
 #include <type_traits>
 #include "rtr_internal.cuh"
 #include "dense.cuh"
-#include "als_tile.cuh"
 
 size_t contract_partial_elems(int num_sms, int64_t I, int C);
 
@@ -103,87 +102,75 @@ __global__ void trace_kernel(const double* __restrict__ M, int n, double* __rest
     }
 }
 
-// ---- fused subchain + contraction -------------------------------------------
-// W[i_n, (beta, alpha)] = sum_j P_<n>[i_n, j] S_j[beta, alpha] with the
-// subchain S_j = Z_{c_1}(i_{c_1}) ... Z_{c_{N-1}}(i_{c_{N-1}}) (c_t = n + t mod N)
-// generated on the fly: a CTA takes prefix indices (i_{c_1} .. i_{c_{N-2}}),
-// forms their product M (R_{n+1} x R_{c_{N-1}}) in shared memory, then for
-// blocks of the last index forms S rows = M Z_last(i) and accumulates the
-// outer products with the matching P entries.  One float64 partial per CTA.
-struct AlsContractArgs {
-    const void* P;
+// ---- subchain of a core update (Eq. 2) ---------------------------------------
+// S[r, beta, alpha] = [Z_{c_1}(i_{c_1}) ... Z_{c_{N-1}}(i_{c_{N-1}})]_{beta alpha}
+// (c_t = n + t mod N), with the row r = a*B + b the natural row-major index of
+// the other modes in the (A, K_n, B) view of P, so that
+//     W = P_<n> S,   W[i_n, (beta, alpha)] = sum_{a,b} P[a, i_n, b] S[a*B + b, (beta, alpha)]
+// is a plain split-K contraction along P's own layout.  A CTA takes prefix
+// indices (i_{c_1} .. i_{c_{N-2}}), forms their product M (R_{n+1} x
+// R_{c_{N-1}}) in shared memory, then writes the rows M Z_last(l) for every
+// index l of the last mode (the cores are staged in shared memory first).
+struct AlsChainArgs {
     const void* Z[RTR_MAXN];          // cores in the compute type T
     int64_t K[RTR_MAXN];
-    int64_t stride[RTR_MAXN];
+    int64_t nstride[RTR_MAXN];        // stride of mode m in the row index r (m != n)
     int R[RTR_MAXN];
     int cyc[RTR_MAXN];
     int N, n;
     int64_t Jpre;
-    double* partial;
-    int stage;                        // 1: the other cores are copied to shared memory first
+    void* S;                          // rows x (R_{n+1} R_n) in T
 };
 
-constexpr int ALS_LB = 16;          // last-mode indices per block
-constexpr int ALS_MAXACC = 40;      // outputs per thread: K_n * C <= 256 * 40
-
 template <typename T>
-__global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs a) {
+__global__ void __launch_bounds__(256) als_subchain_kernel(const AlsChainArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, N = a.N;
     const int Rb = a.R[(n + 1) % N], Rn = a.R[n];
     const int C = Rb * Rn;
-    const int Kn = (int)a.K[n];
     const int ml = a.cyc[N - 1];
     const int Kl = (int)a.K[ml];
     const int Rl = a.R[ml];                         // left rank of the last core
-    T* M0 = reinterpret_cast<T*>(smem_raw);          // Rb x 16
-    T* M1 = M0 + Rb * RTR_MAX_RANK;                  // Rb x 16
-    const int Cp = rtr::tile_cp(C);
-    T* S = M1 + Rb * RTR_MAX_RANK;                   // ALS_LB x Cp
-    T* Pv = S + ALS_LB * Cp;                         // ALS_LB x Kn
-    const T* P = reinterpret_cast<const T*>(a.P);
+    T* M0 = reinterpret_cast<T*>(smem_raw);          // Rb x RTR_MAX_RANK
+    T* M1 = M0 + Rb * RTR_MAX_RANK;
     const int tid = threadIdx.x;
-    // the other cores, read many times per prefix: shared memory (if they fit)
-    // instead of chains of dependent global loads
     const T* Zc[RTR_MAXN];
     {
-        T* zs = Pv + ALS_LB * Kn;
+        T* zs = M1 + Rb * RTR_MAX_RANK;
         for (int t = 1; t < N; ++t) {
             const int m = a.cyc[t];
             const T* src = reinterpret_cast<const T*>(a.Z[m]);
-            if (a.stage) {
-                const int cnt = (int)(a.R[m] * a.K[m] * a.R[(m + 1) % N]);
-                for (int e = tid; e < cnt; e += blockDim.x) zs[e] = src[e];
-                Zc[m] = zs;
-                zs += cnt;
-            } else {
-                Zc[m] = src;
-            }
+            const int cnt = (int)(a.R[m] * a.K[m] * a.R[(m + 1) % N]);
+            for (int e = tid; e < cnt; e += blockDim.x) zs[e] = src[e];
+            Zc[m] = zs;
+            zs += cnt;
         }
-        __syncthreads();
     }
-    const rtr::WTile wt = rtr::wtile(C, Kn);
-    T acc[rtr::TILE_IP][4];
-    rtr::wtile_zero(acc);
-
+    // thread -> (column c, row phase lr): lanes of a row cover C rounded up to 32
+    const int Cp = (C + 31) & ~31;
+    const int rows_pass = max(1, (int)blockDim.x / Cp);
+    const int c = tid % Cp, lr = tid / Cp;
+    const bool active = c < C && lr < rows_pass;
+    const int be = c / Rn, al = c % Rn;
+    T* S = reinterpret_cast<T*>(a.S);
+    const int64_t ls = a.nstride[ml];
     for (int64_t jp = blockIdx.x; jp < a.Jpre; jp += gridDim.x) {
-        // decode the prefix (row-major over c_1 .. c_{N-2}) and its P offset
-        int64_t rem = jp, base = 0;
+        // decode the prefix (row-major over c_1 .. c_{N-2}) and its row offset
+        int64_t rem = jp, rbase = 0;
         int idx[RTR_MAXN];
         for (int t = N - 2; t >= 1; --t) {
             const int m = a.cyc[t];
             idx[t] = (int)(rem % a.K[m]);
             rem /= a.K[m];
-            base += idx[t] * a.stride[m];
+            rbase += idx[t] * a.nstride[m];
         }
-        // M = Z_{c_1}(i_1) ... Z_{c_{N-2}}(i_{N-2})
-        __syncthreads();
+        __syncthreads();                             // staged cores ready / previous M consumed
         {
             const int m = a.cyc[1];
             const int Rc = a.R[(m + 1) % N];
             for (int e = tid; e < Rb * Rc; e += blockDim.x) {
-                const int be = e / Rc, g = e % Rc;
-                M0[be * RTR_MAX_RANK + g] = Zc[m][((int64_t)be * a.K[m] + idx[1]) * Rc + g];
+                const int b2 = e / Rc, g = e % Rc;
+                M0[b2 * RTR_MAX_RANK + g] = Zc[m][((int64_t)b2 * a.K[m] + idx[1]) * Rc + g];
             }
         }
         T* cur = M0;
@@ -193,77 +180,71 @@ __global__ void __launch_bounds__(256) als_contract_kernel(const AlsContractArgs
             const int m = a.cyc[t];
             const int Rm = a.R[m], Rc = a.R[(m + 1) % N];
             for (int e = tid; e < Rb * Rc; e += blockDim.x) {
-                const int be = e / Rc, g = e % Rc;
+                const int b2 = e / Rc, g = e % Rc;
                 T sum = T(0);
-                for (int c = 0; c < Rm; ++c)
-                    sum = fma(cur[be * RTR_MAX_RANK + c], Zc[m][((int64_t)c * a.K[m] + idx[t]) * Rc + g], sum);
-                nxt[be * RTR_MAX_RANK + g] = sum;
+                for (int q = 0; q < Rm; ++q)
+                    sum = fma(cur[b2 * RTR_MAX_RANK + q], Zc[m][((int64_t)q * a.K[m] + idx[t]) * Rc + g], sum);
+                nxt[b2 * RTR_MAX_RANK + g] = sum;
             }
             T* tmp = cur; cur = nxt; nxt = tmp;
         }
         __syncthreads();
-        for (int l0 = 0; l0 < Kl; l0 += ALS_LB) {
-            const int lb = min(ALS_LB, Kl - l0);
-            // S[l][(beta, alpha)] = sum_g M[beta][g] Z_last[g, l0 + l, alpha]  (zero padding to Cp)
-            for (int e = tid; e < lb * Cp; e += blockDim.x) {
-                const int l = e / Cp, c = e % Cp;
+        if (active) {
+            const T* zl = Zc[ml] + al;
+            const int64_t zstride = (int64_t)Kl * Rn;
+            for (int l = lr; l < Kl; l += rows_pass) {
                 T sum = T(0);
-                if (c < C) {
-                    const int be = c / Rn, al = c % Rn;
-                    const T* zl = Zc[ml] + (int64_t)(l0 + l) * Rn + al;
-                    const int64_t zs = (int64_t)Kl * Rn;
-                    for (int g = 0; g < Rl; ++g) sum = fma(cur[be * RTR_MAX_RANK + g], zl[g * zs], sum);
-                }
-                S[e] = sum;
+                for (int g = 0; g < Rl; ++g) sum = fma(cur[be * RTR_MAX_RANK + g], zl[g * zstride + (int64_t)l * Rn], sum);
+                S[(rbase + l * ls) * C + c] = sum;
             }
-            for (int e = tid; e < lb * Kn; e += blockDim.x) {
-                const int l = e / Kn, i = e % Kn;
-                Pv[e] = P[base + (int64_t)(l0 + l) * a.stride[ml] + (int64_t)i * a.stride[n]];
-            }
-            __syncthreads();
-            rtr::wtile_accum(acc, wt, Pv, Kn, S, Cp, lb);
-            __syncthreads();
         }
     }
-    rtr::wtile_store(acc, wt, Kn, C, a.partial + (int64_t)blockIdx.x * Kn * C);
-}
-
-// W[e] = sum of the CTA partials (one warp per output, fixed order)
-__global__ void als_reduce_kernel(const double* __restrict__ partial, int nparts, int count, double* __restrict__ W) {
-    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (e >= count) return;
-    double s = 0.0;
-    for (int q = lane; q < nparts; q += 32) s += partial[(int64_t)q * count + e];
-    s = rtr::warp_sum(s);
-    if (lane == 0) W[e] = s;
 }
 
 // Mprod = E_{s} E_{s+1} ... (cyclic, cnt factors), one CTA per output row:
-// the row is carried through the chain in shared memory (float64).
+// the row is carried through the chain in shared memory (float64); each
+// product splits the sum over l across 8 thread slices (independent load
+// chains), reduced in shared memory in a fixed order.
 struct GramChainArgs {
     const double* E[RTR_MAXN];
     int R[RTR_MAXN];
     int N, start, cnt;
     double* out;
+    float* outf;              // optional float32 copy of out (converted here, on 100 SMs, not
+                              // in the single-CTA inverse: float64 conversions are slow)
     int reindex, Rb, Rn;      // reindex: write G[(b, a), (b', a')] = M[(b, b'), (a, a')]
 };
-__global__ void __launch_bounds__(256) gram_chain_kernel(const GramChainArgs g) {
+constexpr int GC_THREADS = 1024;
+constexpr int GC_COLS = GC_THREADS / 8;
+__global__ void __launch_bounds__(GC_THREADS) gram_chain_kernel(const GramChainArgs g) {
     __shared__ double v0[256], v1[256];
+    __shared__ double part[8][GC_COLS];
     const int r = blockIdx.x;
+    const int tid = threadIdx.x, jl = tid % GC_COLS, q = tid / GC_COLS;
     int m = g.start % g.N;
     int len = g.R[(m + 1) % g.N] * g.R[(m + 1) % g.N];
-    for (int j = threadIdx.x; j < len; j += blockDim.x) v0[j] = g.E[m][(int64_t)r * len + j];
+    for (int j = tid; j < len; j += blockDim.x) v0[j] = g.E[m][(int64_t)r * len + j];
     double* cur = v0;
     double* nxt = v1;
     for (int t = 1; t < g.cnt; ++t) {
         __syncthreads();
         m = (g.start + t) % g.N;
         const int cols = g.R[(m + 1) % g.N] * g.R[(m + 1) % g.N];
-        for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+        const double* Em = g.E[m];
+        for (int j0 = 0; j0 < cols; j0 += GC_COLS) {
+            const int j = j0 + jl;
             double s = 0.0;
-            for (int l = 0; l < len; ++l) s += cur[l] * g.E[m][(int64_t)l * cols + j];
-            nxt[j] = s;
+            if (j < cols)
+                for (int l = q; l < len; l += 8) s = fma(cur[l], Em[(int64_t)l * cols + j], s);
+            part[q][jl] = s;
+            __syncthreads();
+            if (q == 0 && j < cols) {
+                double t2 = part[0][jl];
+#pragma unroll
+                for (int u = 1; u < 8; ++u) t2 += part[u][jl];
+                nxt[j] = t2;
+            }
+            __syncthreads();
         }
         double* tmp = cur; cur = nxt; nxt = tmp;
         len = cols;
@@ -274,7 +255,9 @@ __global__ void __launch_bounds__(256) gram_chain_kernel(const GramChainArgs g) 
         const int be = r / g.Rb, be2 = r % g.Rb;
         for (int j = threadIdx.x; j < len; j += blockDim.x) {
             const int al = j / g.Rn, al2 = j % g.Rn;
-            g.out[(int64_t)(be * g.Rn + al) * C + be2 * g.Rn + al2] = cur[j];
+            const int64_t o = (int64_t)(be * g.Rn + al) * C + be2 * g.Rn + al2;
+            g.out[o] = cur[j];
+            if (g.outf) g.outf[o] = (float)cur[j];
         }
     } else {
         for (int j = threadIdx.x; j < len; j += blockDim.x) g.out[(int64_t)r * len + j] = cur[j];
@@ -286,187 +269,193 @@ __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ 
         b[e] = (float)a[e];
 }
 
-// single CTA: refresh the float32 shadow if the slow path ran, then clear its flag
-__global__ void shadow_if_slow_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n,
-                                      int* __restrict__ slow_ran) {
-    __shared__ int ran;
-    if (threadIdx.x == 0) ran = *(volatile int*)slow_ran;
-    __syncthreads();
-    if (!ran) return;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) b[e] = (float)a[e];
-    __syncthreads();
-    if (threadIdx.x == 0) *slow_ran = 0;
-}
-
-// G[c][c'] of the update of core n from the transfer product (reindexing
-// (beta, beta'), (alpha, alpha') -> (beta, alpha), (beta', alpha')).
-__device__ __forceinline__ double gram_at(const double* __restrict__ Mprod, int Rn, int Rn1, int c, int c2) {
-    const int be = c / Rn, al = c % Rn, be2 = c2 / Rn, al2 = c2 % Rn;
-    return Mprod[((int64_t)be * Rn1 + be2) * (Rn * Rn) + al * Rn + al2];
-}
-
 constexpr int SOLVE_MAXC = 160;       // R_n R_{n+1} <= 144
 
-// Fast path of the core update: one CTA per slice i of mode n solves
-// G z_i = w_i by mixed-precision iterative refinement (Wilkinson; Moler
-// 1967).  G (float64, already in (beta, alpha) order) is equilibrated,
-// D G D with D = diag(G)^-1/2 in float32, and factored by Cholesky in float32
-// (1024 threads: the factorisation is a chain of C barrier-separated steps
-// whose latency needs many warps).  Each refinement step forms the residual
-// w - G z in float64 from the packed Gram matrix in shared memory and adds
-// D (L L^T)^-1 D r (one warp, triangular solves), until ||dz|| <= sqrt(tol2)
-// ||z||, the corrections stop shrinking (the float64 rounding floor), or
-// max_it steps.  If a float32 pivot is not positive the CTA raises
-// *need_slow and the float64 slow path takes over.
-// Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
-constexpr int SOLVE_THREADS = 1024;
-
-__global__ void __launch_bounds__(SOLVE_THREADS) als_solve_fast_kernel(
-    const double* __restrict__ G, int Rn, int Rn1, int In, const double* __restrict__ W,
-    double* __restrict__ Zn, float* __restrict__ Znf, double* __restrict__ zw_out, int* __restrict__ need_slow,
-    int* __restrict__ flags, double tol2, int max_it) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int C = Rn * Rn1;
-    const int ld = C + 1;
-    const size_t msz = ((size_t)C * ld + 3) & ~(size_t)3;
-    float* Ls = reinterpret_cast<float*>(smem_raw);                  // C x ld: Cholesky factor
-    double* Gp = reinterpret_cast<double*>(Ls + msz);                // packed upper Gram (float64)
-    double* z = Gp + (((size_t)C * (C + 1) / 2 + 1) & ~(size_t)1);
-    double* w = z + C;
-    double* r = w + C;
-    float* sc = reinterpret_cast<float*>(r + C);
-    float* invd = sc + C;
-    int* base = reinterpret_cast<int*>(invd + C);
-    __shared__ double red[32];
-    __shared__ int conv;
-    const int i = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tid & 15, ty = tid >> 4, nty = blockDim.x >> 4;
-#ifdef RTR_DEBUG_ITERS
-    long long t_0 = clock64(), t_1 = 0, t_2 = 0;
-#endif
-    (void)flags;
-
-    for (int c = tid; c < C; c += blockDim.x) {
-        const float d = (float)G[(int64_t)c * C + c];
-        sc[c] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 0.f;
-        w[c] = W[(int64_t)i * C + c];
-        z[c] = 0.0;
-        base[c] = c * C - c * (c - 1) / 2;
-    }
-    __syncthreads();
+// Inverse of the Gram matrix of one core update, once per update (one CTA,
+// run on the plan's side stream so that it overlaps the contraction).
+// G (its float32 copy, C x C, (beta, alpha) order) is equilibrated, A = D G D with
+// D = diag(G)^-1/2 in float32, and inverted in place by the sweep operator
+// (Goodnight 1979): sweeping pivot k maps
+//     a_kk -> -1/a_kk,  a_ik -> a_ik/a_kk,  a_kj -> a_kj/a_kk,
+//     a_ij -> a_ij - a_ik a_kj / a_kk          (i, j != k),
+// and sweeping every pivot of a positive definite A leaves -A^-1.  The pivots
+// are the Schur-complement diagonals, i.e. the squared Cholesky pivots, so a
+// pivot that is not positive means A is not numerically positive definite:
+// the kernel then raises *need_slow and writes nothing (the float64 slow path
+// takes over).  Writes Ginv = D A^-1 D (float32, C x C).
+//
+// 256 threads as a 16 x 16 grid; thread (ti, tj) keeps in registers the
+// elements (ti + 16 m, tj + 16 m'), m, m' < T (T = ceil(C / 16) <= 9), so a
+// pivot step costs T^2 register FMAs and 2T shared loads per thread; the
+// pivot column travels through a double-buffered shared vector (one barrier
+// per pivot).
+template <int T>
+__global__ void __launch_bounds__(256) gram_inverse_kernel(const float* __restrict__ G, int C,
+                                                           float* __restrict__ Ginv, int* __restrict__ need_slow) {
+    __shared__ float v[2][16 * T];
+    __shared__ float sc[16 * T];
+    const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
     int ok = 1;
-    for (int c = tid; c < C; c += blockDim.x) if (!(sc[c] > 0.f)) ok = 0;
-    for (int c = ty; c < C; c += nty) {
-        const double* grow = G + (int64_t)c * C;
-        for (int c2 = tx; c2 < C; c2 += 16) {
-            const double g = grow[c2];
-            const float gs = (float)g * sc[c] * sc[c2];
-            if (!isfinite(gs)) ok = 0;
-            Ls[c * ld + c2] = gs;
-            if (c2 >= c) Gp[base[c] + c2 - c] = g;
+    for (int c = tid; c < 16 * T; c += blockDim.x) {
+        float s = 0.f;
+        if (c < C) {
+            const float d = G[(int64_t)c * C + c];
+            s = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 0.f;
+            if (!(s > 0.f)) ok = 0;
         }
+        sc[c] = s;
     }
     ok = __syncthreads_and(ok);
-#ifdef RTR_DEBUG_ITERS
-    t_1 = clock64();
-#endif
-    if (ok) ok = rtr::block_cholesky<float>(Ls, C, ld) ? 1 : 0;
-#ifdef RTR_DEBUG_ITERS
-    t_2 = clock64();
-#endif
     if (!ok) {
         if (tid == 0) atomicExch(need_slow, 1);
         return;
     }
-    for (int c = tid; c < C; c += blockDim.x) invd[c] = 1.0f / Ls[c * ld + c];
-    __syncthreads();
-    double dz2_prev = 0.0;
-    int used = 0;
-    for (int it = 0; it < max_it; ++it) {
-        used = it + 1;
-        // r = G z in float64 (four adjacent lanes per row, packed upper storage)
-        if (it > 0) {
-            for (int e0 = warp * 32; e0 < 4 * C; e0 += blockDim.x) {
-                const int e = e0 + lane;
-                const int c2 = e >> 2, q = e & 3;
-                double acc = 0.0;
-                if (c2 < C) {
-                    for (int c = q; c < c2; c += 4) acc += z[c] * Gp[base[c] + c2 - c];
-                    const double* row = Gp + base[c2] - c2;
-                    for (int c = c2 + ((q - c2) & 3); c < C; c += 4) acc += z[c] * row[c];
-                }
-                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                if (c2 < C && q == 0) r[c2] = acc;
+    float a[T][T];
+#pragma unroll
+    for (int m = 0; m < T; ++m) {
+#pragma unroll
+        for (int mm = 0; mm < T; ++mm) {
+            const int r = ti + 16 * m, c = tj + 16 * mm;
+            float x = 0.f;
+            if (r < C && c < C) {
+                // the upper triangle (min, max) for both (r, c) and (c, r): exactly symmetric
+                const int lo = min(r, c), hi = max(r, c);
+                x = (G[(int64_t)lo * C + hi] * sc[lo]) * sc[hi];
+                if (!isfinite(x)) ok = 0;
+            }
+            a[m][mm] = x;
+        }
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (tid == 0) atomicExch(need_slow, 1);
+        return;
+    }
+    int buf = 0;
+#pragma unroll
+    for (int M = 0; M < T; ++M) {
+        if (16 * M >= C) break;
+        for (int kk = 0; kk < 16; ++kk) {
+            const int k = 16 * M + kk;
+            if (k >= C) break;
+            // owners of column k publish it (padding rows hold 0)
+            if (tj == kk) {
+#pragma unroll
+                for (int m = 0; m < T; ++m) v[buf][ti + 16 * m] = a[m][M];
             }
             __syncthreads();
+            const float d = v[buf][k];
+            if (!(d > 0.f) || !isfinite(d)) {          // same value in every thread: uniform exit
+                if (tid == 0) atomicExch(need_slow, 1);
+                return;
+            }
+            float inv;                                     // hardware reciprocal: the refinement absorbs its error
+            asm("rcp.approx.f32 %0, %1;" : "=f"(inv) : "f"(d));
+            float vi[T], vj[T];
+#pragma unroll
+            for (int m = 0; m < T; ++m) {
+                vi[m] = v[buf][ti + 16 * m] * inv;
+                vj[m] = v[buf][tj + 16 * m];
+            }
+#pragma unroll
+            for (int m = 0; m < T; ++m) {
+#pragma unroll
+                for (int mm = 0; mm < T; ++mm) a[m][mm] = fmaf(-vi[m], vj[mm], a[m][mm]);
+            }
+            // column k and row k of the sweep (2 lanes per warp, resp. one warp)
+            if (tj == kk) {
+#pragma unroll
+                for (int m = 0; m < T; ++m) a[m][M] = vi[m];
+            }
+            if (ti == kk) {
+#pragma unroll
+                for (int mm = 0; mm < T; ++mm) a[M][mm] = vj[mm] * inv;
+                if (tj == kk) a[M][M] = -inv;
+            }
+            buf ^= 1;
         }
-        if (warp == 0) {
-            // (L L^T) y = D (w - G z) in float32: one warp, the vector spread over lanes
-            float y[SOLVE_MAXC / 32];
+    }
 #pragma unroll
-            for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
-                const int j = lane + 32 * t;
-                y[t] = (j < C) ? (float)(it > 0 ? w[j] - r[j] : w[j]) * sc[j] : 0.f;
-            }
+    for (int m = 0; m < T; ++m) {
 #pragma unroll
-            for (int ks = 0; ks < SOLVE_MAXC / 32; ++ks) {
-                for (int kk = 0; kk < 32; ++kk) {
-                    const int k = ks * 32 + kk;
-                    if (k >= C) break;
-                    const float yk = __shfl_sync(0xffffffffu, y[ks], kk) * invd[k];
-                    if (lane == kk) y[ks] = yk;
-#pragma unroll
-                    for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
-                        const int j = lane + 32 * t;
-                        if (j > k && j < C) y[t] -= Ls[j * ld + k] * yk;
-                    }
-                }
-            }
-#pragma unroll
-            for (int ks = SOLVE_MAXC / 32 - 1; ks >= 0; --ks) {
-                for (int kk = 31; kk >= 0; --kk) {
-                    const int k = ks * 32 + kk;
-                    if (k >= C) continue;
-                    const float xk = __shfl_sync(0xffffffffu, y[ks], kk) * invd[k];
-                    if (lane == kk) y[ks] = xk;
-#pragma unroll
-                    for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
-                        const int j = lane + 32 * t;
-                        if (j < k) y[t] -= Ls[k * ld + j] * xk;
-                    }
-                }
-            }
-            double dz2 = 0.0, z2 = 0.0;
-#pragma unroll
-            for (int t = 0; t < SOLVE_MAXC / 32; ++t) {
-                const int j = lane + 32 * t;
-                if (j < C) {
-                    const double dz = (double)(y[t] * sc[j]);
-                    const double zn = z[j] + dz;
-                    z[j] = zn;
-                    dz2 += dz * dz;
-                    z2 += zn * zn;
-                }
-            }
-            dz2 = rtr::warp_sum(dz2);
-            z2 = rtr::warp_sum(z2);
-            if (lane == 0) conv = (dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25 * dz2_prev)) ? 1 : 0;
-            dz2_prev = dz2;
+        for (int mm = 0; mm < T; ++mm) {
+            const int r = ti + 16 * m, c = tj + 16 * mm;
+            if (r < C && c < C) Ginv[(int64_t)r * C + c] = -a[m][mm] * sc[r] * sc[c];
+        }
+    }
+}
+
+// Core update for slice i of mode n (one CTA per slice): z_i solves
+// G z_i = w_i by iterative refinement (Wilkinson; Moler 1967) with the
+// float32 inverse from gram_inverse_kernel:
+//     z <- z + Ginv (w - G z),     residual in float64,
+// until ||dz|| <= sqrt(tol2) ||z||, the corrections stop shrinking (the
+// float64 rounding floor), or max_it steps.  Skips the slice if the inverse
+// raised *need_slow (the slow path solves every slice then).
+// Ginv is staged in shared memory; each product is split over the 8 lanes of
+// an aligned lane group (output c = group), which keeps 8 independent load
+// chains in flight per output.  Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
+constexpr int SOLVE_THREADS = 1024;
+
+__global__ void __launch_bounds__(SOLVE_THREADS) als_solve_inv_kernel(
+    const double* __restrict__ G, const float* __restrict__ Ginv, int Rn, int Rn1, int In,
+    const double* __restrict__ W, double* __restrict__ Zn, float* __restrict__ Znf, double* __restrict__ zw_out,
+    const int* __restrict__ need_slow, double tol2, int max_it) {
+    extern __shared__ __align__(16) float gi[];          // C x C
+    __shared__ double w[SOLVE_MAXC], z[SOLVE_MAXC], dzs[SOLVE_MAXC];
+    __shared__ float rf[SOLVE_MAXC];         // float32 copy of r: one conversion per entry
+    __shared__ double red[32];
+    if (*(volatile const int*)need_slow) return;
+    const int C = Rn * Rn1;
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x, q = tid & 7, grp = tid >> 3, ngrp = SOLVE_THREADS / 8;
+    for (int e = tid; e < C * C; e += SOLVE_THREADS) gi[e] = Ginv[e];
+    for (int c = tid; c < C; c += SOLVE_THREADS) {
+        w[c] = W[(int64_t)i * C + c];
+        z[c] = 0.0;
+        rf[c] = (float)w[c];
+    }
+    __syncthreads();
+    double dz2_prev = 0.0;
+    for (int it = 0; it < max_it; ++it) {
+        // dz = Ginv r (float32; rows of the symmetric inverse read as columns)
+        for (int c0 = 0; c0 < C; c0 += ngrp) {          // every lane reaches the shuffles
+            const int c = c0 + grp;
+            float acc = 0.f;
+            if (c < C)
+                for (int l = q; l < C; l += 8) acc = fmaf(gi[l * C + c], rf[l], acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (q == 0 && c < C) dzs[c] = (double)acc;
         }
         __syncthreads();
-        if (conv) break;
+        double dz = 0.0, zn = 0.0;
+        if (tid < C) {
+            dz = dzs[tid];
+            zn = z[tid] + dz;
+            z[tid] = zn;
+        }
+        const double dz2 = rtr::block_sum(dz * dz, red);  // synchronises: z complete
+        const double z2 = rtr::block_sum(zn * zn, red);
+        const bool conv = dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25 * dz2_prev);
+        dz2_prev = dz2;
+        if (conv || it + 1 == max_it) break;              // uniform: every thread has the same sums
+        // r = w - G z in float64 (G from global memory, coalesced within a lane group)
+        for (int c0 = 0; c0 < C; c0 += ngrp) {
+            const int c = c0 + grp;
+            double acc = 0.0;
+            if (c < C)
+                for (int l = q; l < C; l += 8) acc = fma(G[(int64_t)c * C + l], z[l], acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (q == 0 && c < C) rf[c] = (float)(w[c] - acc);
+        }
+        __syncthreads();
     }
-#ifdef RTR_DEBUG_ITERS
-    if (tid == 0 && blockIdx.x == 0)
-        printf("refine iters %d C=%d build %lld chol %lld iters %lld clk\n", used, C, t_1 - t_0, t_2 - t_1,
-               clock64() - t_2);
-#else
-    (void)used;
-#endif
     double zw = 0.0;
-    for (int c = tid; c < C; c += blockDim.x) {
+    for (int c = tid; c < C; c += SOLVE_THREADS) {
         const int be = c / Rn, al = c % Rn;
         const int64_t o = ((int64_t)al * In + i) * Rn1 + be;
         Zn[o] = z[c];
@@ -488,26 +477,21 @@ __global__ void als_err_kernel(const double* __restrict__ zw, int In, const doub
     }
 }
 
-// Slow path (runs only if the fast path raised *need_slow): float64
+// Slow path (runs only if the Gram inverse raised *need_slow): float64
 // Cholesky of G in shared memory and direct solves, or, if G is not SPD in
 // float64 either, the eigen-pseudo-inverse with cutoff 1e-13 lambda_max
 // (Jacobi eigendecomposition in global scratch).
 __global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __restrict__ Mprod, int Rn, int Rn1,
                                                              int In, const double* __restrict__ W,
                                                              double* __restrict__ Wz, double* __restrict__ Zn,
-                                                             double* __restrict__ zw_out, double* __restrict__ jac_ws,
-                                                             int* __restrict__ need_slow, int* __restrict__ flags,
-                                                             int reset) {
+                                                             float* __restrict__ Znf, double* __restrict__ zw_out,
+                                                             double* __restrict__ jac_ws, int* __restrict__ need_slow,
+                                                             int* __restrict__ flags) {
     if (*(volatile int*)need_slow == 0) return;
     extern __shared__ __align__(16) double Gs[];
     const int C = Rn * Rn1;
     const int ld = C + 1;
-    __shared__ double red[32];
-    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
-        const int c = e / C, c2 = e % C;
-        const int be = c / Rn, al = c % Rn, be2 = c2 / Rn, al2 = c2 % Rn;
-        Gs[c * ld + c2] = Mprod[(int64_t)c * C + c2]; (void)be; (void)al; (void)be2; (void)al2;
-    }
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Gs[(e / C) * ld + e % C] = Mprod[e];
     for (int e = threadIdx.x; e < In * C; e += blockDim.x) Wz[e] = W[e];
     __syncthreads();
     int ok = 1;
@@ -526,11 +510,7 @@ __global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __res
         double* V = jac_ws + (int64_t)C * C;
         __shared__ int pairs[2 * 160];
         __shared__ double cs[2 * 160];
-        for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
-            const int c = e / C, c2 = e % C;
-            const int be = c / Rn, al = c % Rn, be2 = c2 / Rn, al2 = c2 % Rn;
-            Aj[e] = Mprod[(int64_t)c * C + c2]; (void)be; (void)al; (void)be2; (void)al2;
-        }
+        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Aj[e] = Mprod[e];
         __syncthreads();
         rtr::block_jacobi_eig(Aj, V, C, C, pairs, cs, 40);
         double lmax = 0.0;
@@ -558,6 +538,7 @@ __global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __res
         const int i = e / C, c = e % C;
         const int be = c / Rn, al = c % Rn;
         Zn[((int64_t)al * In + i) * Rn1 + be] = Wz[e];
+        if (Znf) Znf[((int64_t)al * In + i) * Rn1 + be] = (float)Wz[e];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < In; i += blockDim.x) {
@@ -566,7 +547,7 @@ __global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __res
         zw_out[i] = zw;
     }
     __syncthreads();
-    if (reset && threadIdx.x == 0) *need_slow = 0;    // else the shadow refresh clears it
+    if (threadIdx.x == 0) *need_slow = 0;
 }
 
 // Default start: entry e of core n is the fp64 table value at field e % 20 of
@@ -744,6 +725,14 @@ T* build_chain(int N, const int64_t* dims, const int* R, const double* const* Z,
     return cur;
 }
 
+int launch_gram_inverse(const float* G, int C, float* Ginv, int* need_slow, cudaStream_t s) {
+    if (C <= 64) gram_inverse_kernel<4><<<1, 256, 0, s>>>(G, C, Ginv, need_slow);
+    else if (C <= 112) gram_inverse_kernel<7><<<1, 256, 0, s>>>(G, C, Ginv, need_slow);
+    else gram_inverse_kernel<9><<<1, 256, 0, s>>>(G, C, Ginv, need_slow);
+    RTR_LAUNCH_CHECK("gram_inverse_kernel");
+    return RTR_OK;
+}
+
 template <typename T>
 int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* err, cudaStream_t s) {
     const int N = p->N;
@@ -755,6 +744,10 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     double* E[RTR_MAXN];
     for (int n = 0; n < N; ++n) E[n] = ws + n * ESZ;
     double* Mp[2] = {ws + RTR_MAXN * ESZ, ws + (RTR_MAXN + 1) * ESZ};
+    // Mp[1] serves the start's transfer products only; during the sweeps it
+    // holds the float32 inverse of the current Gram matrix
+    float* Ginv = reinterpret_cast<float*>(Mp[1]);
+    float* Gf = Ginv + 160 * 160;                    // float32 copy of the Gram matrix
     double* W = ws + (RTR_MAXN + 2) * ESZ;
     double* Wz = W + p->als_wmax;
     double* jac = Wz + p->als_wmax;              // 2 * 144^2 for the pinv fallback
@@ -835,6 +828,18 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
         for (int n = 0; n < N; ++n) Zt[n] = Z[n];
     }
     cudaStream_t side = p->side;
+    // dynamic shared memory limits, set once for the largest update (a host
+    // API call per launch would pace the whole chain of small kernels)
+    {
+        int cmax = 0;
+        for (int n = 0; n < N; ++n) cmax = std::max(cmax, p->R[n] * p->R[(n + 1) % N]);
+        RTR_CUDA(cudaFuncSetAttribute(als_solve_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(float) * (size_t)cmax * cmax)));
+        RTR_CUDA(cudaFuncSetAttribute(als_solve_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(double) * (size_t)cmax * (cmax + 1))));
+        RTR_CUDA(cudaFuncSetAttribute(als_subchain_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      227 * 1024));
+    }
     for (int sweep = 0; sweep < p->params.sweeps; ++sweep) {
         for (int n = 0; n < N; ++n) {
             const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
@@ -853,67 +858,61 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             GramChainArgs gc{};
             for (int m = 0; m < N; ++m) { gc.E[m] = E[m]; gc.R[m] = p->R[m]; }
             gc.N = N; gc.start = n + 1; gc.cnt = N - 1; gc.out = Mp[0];
-            gc.reindex = 1; gc.Rb = Rn1; gc.Rn = Rn;
-            gram_chain_kernel<<<(unsigned)(Rn1 * Rn1), 256, 0, side>>>(gc);
+            gc.reindex = 1; gc.Rb = Rn1; gc.Rn = Rn; gc.outf = Gf;
+            gram_chain_kernel<<<(unsigned)(Rn1 * Rn1), GC_THREADS, 0, side>>>(gc);
             RTR_LAUNCH_CHECK("gram_chain_kernel");
+            if ((st = launch_gram_inverse(Gf, C, Ginv, need_slow, side))) return st;
             RTR_CUDA(cudaEventRecord(p->ev[1], side));
             // ---- caller's stream: W = P_<n> S, subchain generated in the contraction
-            AlsContractArgs ca{};
-            ca.P = P; ca.N = N; ca.n = n; ca.partial = p->partial;
-            {
-                int64_t st_ = 1;
-                for (int m = N - 1; m >= 0; --m) { ca.stride[m] = st_; st_ *= Kd[m]; }
-            }
+            // ---- caller's stream: subchain S (natural row order), then W = P_<n> S
+            AlsChainArgs ca{};
+            ca.N = N; ca.n = n;
             for (int m = 0; m < N; ++m) { ca.Z[m] = Zt[m]; ca.K[m] = Kd[m]; ca.R[m] = p->R[m]; }
+            for (int m = 0; m < N; ++m) {
+                if (m == n) { ca.nstride[m] = 0; continue; }
+                int64_t ns = (m > n) ? 1 : B;
+                for (int m2 = m + 1; m2 < N; ++m2)
+                    if (m2 != n && (m > n || m2 < n)) ns *= Kd[m2];
+                ca.nstride[m] = ns;
+            }
             for (int t = 0; t < N; ++t) ca.cyc[t] = (n + t) % N;
             ca.Jpre = 1;
             for (int t = 1; t <= N - 2; ++t) ca.Jpre *= Kd[ca.cyc[t]];
-            const int nout = (int)I * C;
-            if (nout > 256 * ALS_MAXACC) return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: K_n R_n R_{n+1} > 10240");
-            int64_t gx = std::min<int64_t>(ca.Jpre, 4 * (int64_t)p->num_sms);
-            gx = std::min<int64_t>(gx, (int64_t)(p->partial_elems / nout));
-            size_t csmem = sizeof(T) * (2 * (size_t)Rn1 * RTR_MAX_RANK + (size_t)ALS_LB * ((C + 3) & ~3) + (size_t)ALS_LB * I);
-            size_t zbytes = 0;
+            if ((size_t)(A * B) * (size_t)C * sizeof(T) > p->sub_bytes)
+                return rtr_set_error(RTR_ENOMEM, "TR-ALS: subchain exceeds the plan workspace");
+            ca.S = p->sub_ws[0];
+            size_t csmem = sizeof(T) * 2 * (size_t)Rn1 * RTR_MAX_RANK;
             for (int t = 1; t < N; ++t) {
                 const int m = (n + t) % N;
-                zbytes += sizeof(T) * (size_t)p->R[m] * Kd[m] * p->R[(m + 1) % N];
+                csmem += sizeof(T) * (size_t)p->R[m] * Kd[m] * p->R[(m + 1) % N];
             }
-            ca.stage = (csmem + zbytes <= 96 * 1024) ? 1 : 0;
-            if (ca.stage) csmem += zbytes;
-            if (csmem > 48 * 1024)
-                RTR_CUDA(cudaFuncSetAttribute(als_contract_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
-            als_contract_kernel<T><<<(unsigned)gx, 256, csmem, s>>>(ca);
-            RTR_LAUNCH_CHECK("als_contract_kernel");
-            als_reduce_kernel<<<(unsigned)rtr_ceil_div((int64_t)nout * 32, 256), 256, 0, s>>>(p->partial, (int)gx, nout, W);
-            RTR_LAUNCH_CHECK("als_reduce_kernel");
+            if (csmem > 227 * 1024) return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: cores exceed shared memory");
+            const int64_t gx = std::min<int64_t>(ca.Jpre, 2 * (int64_t)p->num_sms);
+            als_subchain_kernel<T><<<(unsigned)gx, 256, csmem, s>>>(ca);
+            RTR_LAUNCH_CHECK("als_subchain_kernel");
+            {
+                ContractArgs w{};
+                w.X = P; w.A = A; w.I = I; w.B = B; w.C = C;
+                w.gen = 0; w.M = p->sub_ws[0]; w.ldm = C;
+                w.Y = W; w.norm_out = nullptr;
+                if ((st = launch_contract(p, is_f64, w, s))) return st;
+            }
             // ---- join, then solve G z_i = w_i for every slice
             RTR_CUDA(cudaStreamWaitEvent(s, p->ev[1], 0));
             double* G = Mp[0];
-            const size_t fsmem = sizeof(float) * ((((size_t)C * (C + 1)) + 3) & ~(size_t)3) +
-                                 sizeof(double) * ((((size_t)C * (C + 1) / 2) + 1) & ~(size_t)1) +
-                                 3 * sizeof(double) * C + 3 * sizeof(float) * C;
-            RTR_CUDA(cudaFuncSetAttribute(als_solve_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)fsmem));
             // refinement: float64 accuracy for FP64 plans; for the float32 / BF16
             // plans one float64-residual correction after the float32 solve
             // (relative error ~(kappa 2^-24)^2)
             const double tol2 = is_f64 ? 1e-28 : 1e-18;
             const int max_it = is_f64 ? 12 : 2;
-            als_solve_fast_kernel<<<(unsigned)I, SOLVE_THREADS, fsmem, s>>>(G, Rn, Rn1, (int)I, W, Z[n], Zf[n], zw,
-                                                                           need_slow, p->flags, tol2, max_it);
-            RTR_LAUNCH_CHECK("als_solve_fast_kernel");
+            const size_t gsmem = sizeof(float) * (size_t)C * C;
+            als_solve_inv_kernel<<<(unsigned)I, SOLVE_THREADS, gsmem, s>>>(G, Ginv, Rn, Rn1, (int)I, W, Z[n], Zf[n],
+                                                                          zw, need_slow, tol2, max_it);
+            RTR_LAUNCH_CHECK("als_solve_inv_kernel");
             const size_t ssmem = sizeof(double) * (size_t)C * (C + 1);
-            RTR_CUDA(cudaFuncSetAttribute(als_solve_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)ssmem));
-            als_solve_slow_kernel<<<1, 512, ssmem, s>>>(G, Rn, Rn1, (int)I, W, Wz, Z[n], zw, jac, need_slow,
-                                                        p->flags, is_f64);
+            als_solve_slow_kernel<<<1, 512, ssmem, s>>>(G, Rn, Rn1, (int)I, W, Wz, Z[n], Zf[n], zw, jac,
+                                                        need_slow, p->flags);
             RTR_LAUNCH_CHECK("als_solve_slow_kernel");
-            if (!is_f64) {
-                const int64_t cnt = (int64_t)Rn * I * Rn1;
-                // the slow path (rare) writes only float64 cores: refresh the shadow
-                shadow_if_slow_kernel<<<1, 256, 0, s>>>(Z[n], Zf[n], cnt, need_slow);
-                RTR_LAUNCH_CHECK("shadow_if_slow_kernel");
-            }
             if (err && n == N - 1) {
                 als_err_kernel<<<1, 32, 0, s>>>(zw, (int)I, normP2, err + sweep);
                 RTR_LAUNCH_CHECK("als_err_kernel");
