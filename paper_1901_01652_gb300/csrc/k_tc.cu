@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
     if (warp < CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
+        const bool want_norm = p.normp != nullptr;   // ||X||^2 only in the pass that records it
         Ring rg(S);
         ChunkPos cp(blockIdx.x, gridDim.x, p.nbc);
         for (int64_t t = 0; t < nloc; ++t, rg.step(1), cp.step()) {
@@ -187,7 +188,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
                 const int64_t a0 = ch * KC;
                 const int len = (int)min((int64_t)KC, p.A - a0);
                 const float* xb = p.X + a0 * p.I + rbeg;
-                if (p.vec) {
+                if (p.vec && !p.fp8) {
+                    // item = (quad u4 of rows, quad qq of r values): four coalesced
+                    // float4 loads (lanes run along the contiguous i), a 4 x 4
+                    // transpose in registers, then 8-byte stores of 4 consecutive r
+                    const int U = rows_valid >> 2;
+                    const int nitems = U * (KC / 4);
+                    for (int it0 = 0; it0 < nitems; it0 += CONV_THREADS * 2) {
+                        float4 x[2][4];
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int it = it0 + ct + CONV_THREADS * j;
+                            const int u4 = it % U, qq = it / U;
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                x[j][t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (it < nitems && 4 * qq + t < len)
+                                    x[j][t] = __ldg(reinterpret_cast<const float4*>(xb + (int64_t)(4 * qq + t) * p.I + 4 * u4));
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int it = it0 + ct + CONV_THREADS * j;
+                            if (it >= nitems) continue;
+                            const int u4 = it % U, qq = it / U;
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                const float r0 = (&x[j][0].x)[v], r1 = (&x[j][1].x)[v];
+                                const float r2 = (&x[j][2].x)[v], r3 = (&x[j][3].x)[v];
+                                if (want_norm) csum += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
+                                uint32_t h0, l0, h1, l1;
+                                split2(r0, r1, h0, l0);
+                                split2(r2, r3, h1, l1);
+                                const int row = 4 * u4 + v;
+                                const uint32_t off = (uint32_t)(row >> 7) * MTILE_BYTES + sw128_off(row & 127, 4 * qq);
+                                st_shared_v2(hi_base + off, h0, h1);
+                                st_shared_v2(lo_base + off, l0, l1);
+                            }
+                        }
+                    }
+                } else if (p.vec) {
                     const int nitems = (rows_valid >> 2) * 32;
                     for (int it0 = 0; it0 < nitems; it0 += CONV_THREADS * 4) {
                         float4 x0[4], x1[4];
@@ -471,6 +511,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     if (warp < TM_CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
+        const bool want_norm = p.normp != nullptr;
         Ring rs(S_st), ro(S_op);
         for (int64_t t = 0; t < nloc; ++t, rs.step(1), ro.step(1)) {
             const int ss = rs.slot, so = ro.slot;
@@ -480,9 +521,9 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
             const uint32_t src = st0 + ss * TM_STAGE_X;
             const uint32_t hi = op0 + so * op_bytes, lo = hi + MTILE_BYTES;
             float csum = 0.f;
-            auto piece = [&](const float4 v, int row, int c4) {
-                if (row < rows_valid) csum += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
-                const uint32_t off = sw128_off(row, 4 * c4);
+            auto piece = [&](const float4 v, int row, int c4, uint32_t off) {
+                // ||X||^2 is accumulated only in the pass that records it
+                if (want_norm && row < rows_valid) csum += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
                 if (p.fp8) {
                     // a 32-value scale block is 8 consecutive pieces of one row,
                     // held by 8 consecutive lanes (kc = 32 or 64)
@@ -505,11 +546,11 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     const int pc = ct + TM_CONV_THREADS * j;
                     v[j] = ld_shared_f4(src + (uint32_t)(pc >> 4) * 256u + (uint32_t)(pc & 15) * 16u);
                 }
+                // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15;
+                // the swizzle phase (row & 7) is the same for every j
+                const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int pc = ct + TM_CONV_THREADS * j;
-                    piece(v[j], pc >> 4, pc & 15);
-                }
+                for (int j = 0; j < 8; ++j) piece(v[j], (ct >> 4) + 16 * j, ct & 15, off0 + 2048u * j);
             } else {
                 // kc = 4 Q4 with Q4 a compile-time constant: row/column of a piece
                 // by multiply-shift, loads batched like the full-width case
@@ -526,7 +567,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
 #pragma unroll
                     for (int j = 0; j < NP; ++j) {
                         const int pc = ct + TM_CONV_THREADS * j;
-                        if (pc < 128 * Q4) piece(v[j], pc / Q4, pc % Q4);
+                        if (pc < 128 * Q4) piece(v[j], pc / Q4, pc % Q4, sw128_off(pc / Q4, 4 * (pc % Q4)));
                     }
                 };
                 switch (p.kc >> 2) {

@@ -2,8 +2,11 @@
 //     out[a, k, b] = sum_i X[a, i, b] * Q[i, k]        (X x_n Q^T)
 // in float32 or float64.  A tile is CT consecutive columns (a, b) of the
 // (A, I, B) view (a run of b inside one a, or a run of a when B == 1, so that
-// loads and stores go along the contiguous index).  Q (float64 in memory) is
-// staged in shared memory in the compute type, I in chunks of IC rows.
+// loads and stores go along the contiguous index).  When 1 < B < CT a tile
+// holds floor(CT / B) whole a-blocks instead (column cc -> a = cc / B,
+// b = cc % B from a table in shared memory), so that short fibres (B = 25 in
+// the middle of a chain) do not leave most of the tile empty.  Q (float64 in
+// memory) is staged in shared memory in the compute type, I in chunks of IC rows.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -25,7 +28,12 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
     const int xld = CT + 1;
     T* Qs = reinterpret_cast<T*>(smem_raw);     // [IC][KP]
     T* Xs = Qs + (size_t)IC * KP;              // [IC][xld]
+    int* cmap = reinterpret_cast<int*>(Xs + (size_t)IC * xld);   // [CT] (a << 16) | b, short fibres
     const int tid = threadIdx.x;
+    const bool blocks = B > 1 && B < CT;        // tile = whole a-blocks
+    const int nab = blocks ? CT / (int)B : 0;
+    if (blocks)
+        for (int cc = tid; cc < CT; cc += NT) cmap[cc] = ((cc / (int)B) << 16) | (cc % (int)B);
     const int NCT = CT / TC;
     const int tc = tid % NCT, tko = tid / NCT;
     const int nic = (I + IC - 1) / IC;
@@ -43,6 +51,7 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
         int64_t a0, b0;
         int len;
         if (B == 1) { a0 = t * CT; b0 = 0; len = (int)min((int64_t)CT, A - a0); }
+        else if (blocks) { a0 = t * nab; b0 = 0; len = (int)(min((int64_t)nab, A - a0) * B); }
         else { a0 = t / nbt; b0 = (t % nbt) * CT; len = (int)min((int64_t)CT, B - b0); }
         T acc[TKO][TC];
 #pragma unroll
@@ -57,6 +66,16 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
                 for (int e = tid; e < ic * CT; e += NT) {
                     const int il = e % ic, cc = e / ic;
                     Xs[il * xld + cc] = (cc < len) ? X[(a0 + cc) * (int64_t)I + i0 + il] : T(0);
+                }
+            } else if (blocks) {
+                for (int e = tid; e < ic * CT; e += NT) {
+                    const int cc = e % CT, il = e / CT;
+                    T v = T(0);
+                    if (cc < len) {
+                        const int m = cmap[cc];
+                        v = X[((a0 + (m >> 16)) * I + i0 + il) * B + (m & 0xFFFF)];
+                    }
+                    Xs[il * xld + cc] = v;
                 }
             } else {
                 for (int e = tid; e < ic * CT; e += NT) {
@@ -87,7 +106,10 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
                 const int cc = tc * TC + c;
                 if (cc >= len) continue;
                 if (B == 1) out[(a0 + cc) * (int64_t)K + k] = acc[o][c];
-                else out[(a0 * K + k) * B + b0 + cc] = acc[o][c];
+                else if (blocks) {
+                    const int m = cmap[cc];
+                    out[((a0 + (m >> 16)) * K + k) * B + (m & 0xFFFF)] = acc[o][c];
+                } else out[(a0 * K + k) * B + b0 + cc] = acc[o][c];
             }
         }
     }
@@ -104,9 +126,10 @@ int launch_variant(rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B, con
     // and X chunks within 100 KB so that two CTAs fit on an SM
     const int64_t fit = (int64_t)(100 * 1024) / (int64_t)(sizeof(T) * (nkt * TKO + CT + 1));
     const int IC = (int)std::max<int64_t>(1, std::min<int64_t>({I, sizeof(T) == 8 ? 128 : 256, fit}));
-    const size_t smem = sizeof(T) * ((size_t)IC * nkt * TKO + (size_t)IC * (CT + 1));
+    const size_t smem = sizeof(T) * ((size_t)IC * nkt * TKO + (size_t)IC * (CT + 1)) + sizeof(int) * (size_t)CT;
     int64_t ntiles, nbt = 1;
     if (B == 1) ntiles = rtr_ceil_div(A, CT);
+    else if (B < CT) ntiles = rtr_ceil_div(A, CT / B);      // whole a-blocks per tile
     else { nbt = rtr_ceil_div(B, CT); ntiles = A * nbt; }
     auto kern = ttm_kernel<T, TKO, TC>;
     RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
