@@ -27,35 +27,38 @@ namespace {
 // With final_tr, row j = b*A + a of the cyclic order is stored at a*B + b.
 // With Zfirst set (and Sprev null), the previous level is the first core
 // itself, read in its own layout Zfirst[beta, j', c] (Jp = its mode length).
-template <typename T>
-__global__ void subchain_step_kernel(const T* __restrict__ Sprev, int64_t Jp, int Rb, int Rc,
-                                     const double* __restrict__ Z, int Km, int Rd, T* __restrict__ Sout,
-                                     int final_tr, int64_t Aa, int64_t Bb, const double* __restrict__ Zfirst) {
-    const int64_t total = Jp * Km * Rb * Rd;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int g = (int)(e % Rd);
-        const int be = (int)((e / Rd) % Rb);
-        const int64_t j = e / ((int64_t)Rd * Rb);
-        const int i = (int)(j % Km);
-        const int64_t jp = j / Km;
+// IDX: index type of the element decode (uint32_t when every index fits:
+// a 64-bit division is a long instruction sequence per element)
+template <typename T, typename TZ, typename IDX>
+__global__ void subchain_step_kernel(const T* __restrict__ Sprev, int64_t Jp_, int Rb, int Rc,
+                                     const TZ* __restrict__ Z, int Km, int Rd, T* __restrict__ Sout,
+                                     int final_tr, int64_t Aa_, int64_t Bb_, const TZ* __restrict__ Zfirst) {
+    const IDX Jp = (IDX)Jp_, Aa = (IDX)Aa_, Bb = (IDX)Bb_;
+    const IDX total = Jp * (IDX)Km * (IDX)Rb * (IDX)Rd;
+    for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < total; e += (IDX)gridDim.x * blockDim.x) {
+        const int g = (int)(e % (IDX)Rd);
+        const IDX q = e / (IDX)Rd;
+        const int be = (int)(q % (IDX)Rb);
+        const IDX j = q / (IDX)Rb;
+        const int i = (int)(j % (IDX)Km);
+        const IDX jp = j / (IDX)Km;
         T v;
         if (Zfirst != nullptr) {
             T acc = T(0);
-            const double* zf = Zfirst + ((int64_t)be * Jp + jp) * Rc;
-            for (int c = 0; c < Rc; ++c) acc = fma((T)zf[c], (T)Z[((int64_t)c * Km + i) * Rd + g], acc);
+            const TZ* zf = Zfirst + ((IDX)be * Jp + jp) * (IDX)Rc;
+            for (int c = 0; c < Rc; ++c) acc = fma((T)zf[c], (T)Z[((IDX)c * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)g], acc);
             v = acc;
         } else if (Sprev == nullptr) {
-            v = (T)Z[((int64_t)be * Km + i) * Rd + g];
+            v = (T)Z[((IDX)be * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)g];
         } else {
-            T s = T(0);
-            const T* sp = Sprev + (jp * Rb + be) * Rc;
-            for (int c = 0; c < Rc; ++c) s = fma(sp[c], (T)Z[((int64_t)c * Km + i) * Rd + g], s);
-            v = s;
+            T sum = T(0);
+            const T* sp = Sprev + (jp * (IDX)Rb + (IDX)be) * (IDX)Rc;
+            for (int c = 0; c < Rc; ++c) sum = fma(sp[c], (T)Z[((IDX)c * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)g], sum);
+            v = sum;
         }
-        int64_t r = j;
-        if (final_tr) { const int64_t b = j / Aa, a = j % Aa; r = a * Bb + b; }
-        Sout[(r * Rb + be) * Rd + g] = v;
+        IDX r = j;
+        if (final_tr) { const IDX b = j / Aa, a = j % Aa; r = a * Bb + b; }
+        Sout[(r * (IDX)Rb + (IDX)be) * (IDX)Rd + (IDX)g] = v;
     }
 }
 
@@ -102,105 +105,6 @@ __global__ void trace_kernel(const double* __restrict__ M, int n, double* __rest
     }
 }
 
-// ---- subchain of a core update (Eq. 2) ---------------------------------------
-// S[r, beta, alpha] = [Z_{c_1}(i_{c_1}) ... Z_{c_{N-1}}(i_{c_{N-1}})]_{beta alpha}
-// (c_t = n + t mod N), with the row r = a*B + b the natural row-major index of
-// the other modes in the (A, K_n, B) view of P, so that
-//     W = P_<n> S,   W[i_n, (beta, alpha)] = sum_{a,b} P[a, i_n, b] S[a*B + b, (beta, alpha)]
-// is a plain split-K contraction along P's own layout.  A CTA takes prefix
-// indices (i_{c_1} .. i_{c_{N-2}}), forms their product M (R_{n+1} x
-// R_{c_{N-1}}) in shared memory, then writes the rows M Z_last(l) for every
-// index l of the last mode (the cores are staged in shared memory first).
-struct AlsChainArgs {
-    const void* Z[RTR_MAXN];          // cores in the compute type T
-    int64_t K[RTR_MAXN];
-    int64_t nstride[RTR_MAXN];        // stride of mode m in the row index r (m != n)
-    int R[RTR_MAXN];
-    int cyc[RTR_MAXN];
-    int N, n;
-    int64_t Jpre;
-    void* S;                          // rows x (R_{n+1} R_n) in T
-};
-
-template <typename T>
-__global__ void __launch_bounds__(256) als_subchain_kernel(const AlsChainArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = a.n, N = a.N;
-    const int Rb = a.R[(n + 1) % N], Rn = a.R[n];
-    const int C = Rb * Rn;
-    const int ml = a.cyc[N - 1];
-    const int Kl = (int)a.K[ml];
-    const int Rl = a.R[ml];                         // left rank of the last core
-    T* M0 = reinterpret_cast<T*>(smem_raw);          // Rb x RTR_MAX_RANK
-    T* M1 = M0 + Rb * RTR_MAX_RANK;
-    const int tid = threadIdx.x;
-    const T* Zc[RTR_MAXN];
-    {
-        T* zs = M1 + Rb * RTR_MAX_RANK;
-        for (int t = 1; t < N; ++t) {
-            const int m = a.cyc[t];
-            const T* src = reinterpret_cast<const T*>(a.Z[m]);
-            const int cnt = (int)(a.R[m] * a.K[m] * a.R[(m + 1) % N]);
-            for (int e = tid; e < cnt; e += blockDim.x) zs[e] = src[e];
-            Zc[m] = zs;
-            zs += cnt;
-        }
-    }
-    // thread -> (column c, row phase lr): lanes of a row cover C rounded up to 32
-    const int Cp = (C + 31) & ~31;
-    const int rows_pass = max(1, (int)blockDim.x / Cp);
-    const int c = tid % Cp, lr = tid / Cp;
-    const bool active = c < C && lr < rows_pass;
-    const int be = c / Rn, al = c % Rn;
-    T* S = reinterpret_cast<T*>(a.S);
-    const int64_t ls = a.nstride[ml];
-    for (int64_t jp = blockIdx.x; jp < a.Jpre; jp += gridDim.x) {
-        // decode the prefix (row-major over c_1 .. c_{N-2}) and its row offset
-        int64_t rem = jp, rbase = 0;
-        int idx[RTR_MAXN];
-        for (int t = N - 2; t >= 1; --t) {
-            const int m = a.cyc[t];
-            idx[t] = (int)(rem % a.K[m]);
-            rem /= a.K[m];
-            rbase += idx[t] * a.nstride[m];
-        }
-        __syncthreads();                             // staged cores ready / previous M consumed
-        {
-            const int m = a.cyc[1];
-            const int Rc = a.R[(m + 1) % N];
-            for (int e = tid; e < Rb * Rc; e += blockDim.x) {
-                const int b2 = e / Rc, g = e % Rc;
-                M0[b2 * RTR_MAX_RANK + g] = Zc[m][((int64_t)b2 * a.K[m] + idx[1]) * Rc + g];
-            }
-        }
-        T* cur = M0;
-        T* nxt = M1;
-        for (int t = 2; t <= N - 2; ++t) {
-            __syncthreads();
-            const int m = a.cyc[t];
-            const int Rm = a.R[m], Rc = a.R[(m + 1) % N];
-            for (int e = tid; e < Rb * Rc; e += blockDim.x) {
-                const int b2 = e / Rc, g = e % Rc;
-                T sum = T(0);
-                for (int q = 0; q < Rm; ++q)
-                    sum = fma(cur[b2 * RTR_MAX_RANK + q], Zc[m][((int64_t)q * a.K[m] + idx[t]) * Rc + g], sum);
-                nxt[b2 * RTR_MAX_RANK + g] = sum;
-            }
-            T* tmp = cur; cur = nxt; nxt = tmp;
-        }
-        __syncthreads();
-        if (active) {
-            const T* zl = Zc[ml] + al;
-            const int64_t zstride = (int64_t)Kl * Rn;
-            for (int l = lr; l < Kl; l += rows_pass) {
-                T sum = T(0);
-                for (int g = 0; g < Rl; ++g) sum = fma(cur[be * RTR_MAX_RANK + g], zl[g * zstride + (int64_t)l * Rn], sum);
-                S[(rbase + l * ls) * C + c] = sum;
-            }
-        }
-    }
-}
-
 // Mprod = E_{s} E_{s+1} ... (cyclic, cnt factors), one CTA per output row:
 // the row is carried through the chain in shared memory (float64); each
 // product splits the sum over l across 8 thread slices (independent load
@@ -211,7 +115,8 @@ struct GramChainArgs {
     int N, start, cnt;
     double* out;
     float* outf;              // optional float32 copy of out (converted here, on 100 SMs, not
-                              // in the single-CTA inverse: float64 conversions are slow)
+                              // in the single-CTA kernels: float64 conversions are slow)
+    float* outl;              // optional low part: out - (double)outf, as float32
     int reindex, Rb, Rn;      // reindex: write G[(b, a), (b', a')] = M[(b, b'), (a, a')]
 };
 constexpr int GC_THREADS = 1024;
@@ -257,7 +162,11 @@ __global__ void __launch_bounds__(GC_THREADS) gram_chain_kernel(const GramChainA
             const int al = j / g.Rn, al2 = j % g.Rn;
             const int64_t o = (int64_t)(be * g.Rn + al) * C + be2 * g.Rn + al2;
             g.out[o] = cur[j];
-            if (g.outf) g.outf[o] = (float)cur[j];
+            if (g.outf) {
+                const float h = (float)cur[j];
+                g.outf[o] = h;
+                if (g.outl) g.outl[o] = (float)(cur[j] - (double)h);
+            }
         }
     } else {
         for (int j = threadIdx.x; j < len; j += blockDim.x) g.out[(int64_t)r * len + j] = cur[j];
@@ -388,37 +297,53 @@ __global__ void __launch_bounds__(256) gram_inverse_kernel(const float* __restri
 // Core update for slice i of mode n (one CTA per slice): z_i solves
 // G z_i = w_i by iterative refinement (Wilkinson; Moler 1967) with the
 // float32 inverse from gram_inverse_kernel:
-//     z <- z + Ginv (w - G z),     residual in float64,
+//     z <- z + Ginv (w - G z),
 // until ||dz|| <= sqrt(tol2) ||z||, the corrections stop shrinking (the
-// float64 rounding floor), or max_it steps.  Skips the slice if the inverse
-// raised *need_slow (the slow path solves every slice then).
-// Ginv is staged in shared memory; each product is split over the 8 lanes of
-// an aligned lane group (output c = group), which keeps 8 independent load
-// chains in flight per output.  Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
+// rounding floor of the residual), or max_it steps.  z, w and the residual
+// are kept as unevaluated float pairs (hi + lo, "double-float", Dekker 1971):
+// the residual sum over l of G[c][l] z[l] uses G = Gh + Gl from the Gram
+// kernel, error-free products (fma) and two-sum accumulation, about 2^-44
+// relative to sum |G z|, all on the FP32 pipe (GB300's float64 rate is far
+// lower).  Skips the slice if the inverse raised *need_slow (the slow path
+// solves every slice then).  Ginv is staged in shared memory; each product is
+// split over the 8 lanes of an aligned lane group (output c = group).
+// Writes Z_n[alpha, i, beta] and zw[i] = z_i . w_i.
 constexpr int SOLVE_THREADS = 1024;
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_inv_kernel(
-    const double* __restrict__ G, const float* __restrict__ Ginv, int Rn, int Rn1, int In,
-    const double* __restrict__ W, double* __restrict__ Zn, float* __restrict__ Znf, double* __restrict__ zw_out,
-    const int* __restrict__ need_slow, double tol2, int max_it) {
+    const float* __restrict__ Gh, const float* __restrict__ Gl, const float* __restrict__ Ginv, int Rn, int Rn1,
+    int In, const double* __restrict__ W, double* __restrict__ Zn, float* __restrict__ Znf,
+    double* __restrict__ zw_out, const int* __restrict__ need_slow, float tol2, int max_it) {
     extern __shared__ __align__(16) float gi[];          // C x C
-    __shared__ double w[SOLVE_MAXC], z[SOLVE_MAXC], dzs[SOLVE_MAXC];
-    __shared__ float rf[SOLVE_MAXC];         // float32 copy of r: one conversion per entry
+    __shared__ float wh[SOLVE_MAXC], wl[SOLVE_MAXC], zh[SOLVE_MAXC], zl[SOLVE_MAXC], rf[SOLVE_MAXC];
+    __shared__ float redf[2][32];
     __shared__ double red[32];
     if (*(volatile const int*)need_slow) return;
     const int C = Rn * Rn1;
     const int i = blockIdx.x;
-    const int tid = threadIdx.x, q = tid & 7, grp = tid >> 3, ngrp = SOLVE_THREADS / 8;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = tid & 7, grp = tid >> 3, ngrp = SOLVE_THREADS / 8;
     for (int e = tid; e < C * C; e += SOLVE_THREADS) gi[e] = Ginv[e];
     for (int c = tid; c < C; c += SOLVE_THREADS) {
-        w[c] = W[(int64_t)i * C + c];
-        z[c] = 0.0;
-        rf[c] = (float)w[c];
+        const double wd = W[(int64_t)i * C + c];
+        const float h = (float)wd;
+        wh[c] = h;
+        wl[c] = (float)(wd - (double)h);
+        zh[c] = 0.f;
+        zl[c] = 0.f;
+        rf[c] = h;
     }
     __syncthreads();
-    double dz2_prev = 0.0;
+    float dz2_prev = 0.f;
     for (int it = 0; it < max_it; ++it) {
-        // dz = Ginv r (float32; rows of the symmetric inverse read as columns)
+        // dz = Ginv r (float32; rows of the symmetric inverse read as columns), z += dz
+        float d2 = 0.f, n2 = 0.f;
         for (int c0 = 0; c0 < C; c0 += ngrp) {          // every lane reaches the shuffles
             const int c = c0 + grp;
             float acc = 0.f;
@@ -427,30 +352,58 @@ __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_inv_kernel(
             acc += __shfl_xor_sync(0xffffffffu, acc, 1);
             acc += __shfl_xor_sync(0xffffffffu, acc, 2);
             acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            if (q == 0 && c < C) dzs[c] = (double)acc;
+            if (q == 0 && c < C) {
+                float sh, se;
+                two_sum(zh[c], acc, sh, se);
+                const float lo = zl[c] + se;
+                const float nh = sh + lo;
+                zh[c] = nh;
+                zl[c] = lo - (nh - sh);
+                d2 += acc * acc;
+                n2 += nh * nh;
+            }
         }
-        __syncthreads();
-        double dz = 0.0, zn = 0.0;
-        if (tid < C) {
-            dz = dzs[tid];
-            zn = z[tid] + dz;
-            z[tid] = zn;
-        }
-        const double dz2 = rtr::block_sum(dz * dz, red);  // synchronises: z complete
-        const double z2 = rtr::block_sum(zn * zn, red);
-        const bool conv = dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25 * dz2_prev);
+        // convergence sums (float32 is ample for a stopping test)
+        d2 = rtr::warp_sum(d2);
+        n2 = rtr::warp_sum(n2);
+        if (lane == 0) { redf[0][warp] = d2; redf[1][warp] = n2; }
+        __syncthreads();                                  // z complete, r no longer read
+        float dz2 = 0.f, z2 = 0.f;
+        for (int u = 0; u < SOLVE_THREADS / 32; ++u) { dz2 += redf[0][u]; z2 += redf[1][u]; }
+        const bool conv = dz2 <= tol2 * z2 || (it >= 2 && dz2 > 0.25f * dz2_prev);
         dz2_prev = dz2;
         if (conv || it + 1 == max_it) break;              // uniform: every thread has the same sums
-        // r = w - G z in float64 (G from global memory, coalesced within a lane group)
+        // r = w - G z in double-float
         for (int c0 = 0; c0 < C; c0 += ngrp) {
             const int c = c0 + grp;
-            double acc = 0.0;
-            if (c < C)
-                for (int l = q; l < C; l += 8) acc = fma(G[(int64_t)c * C + l], z[l], acc);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            if (q == 0 && c < C) rf[c] = (float)(w[c] - acc);
+            float S = 0.f, E = 0.f;
+            if (c < C) {
+                const float* gh = Gh + (int64_t)c * C;
+                const float* gl = Gl + (int64_t)c * C;
+                for (int l = q; l < C; l += 8) {
+                    const float a = gh[l], b = zh[l];
+                    const float p = a * b;
+                    const float pe = fmaf(a, b, -p);              // a b = p + pe exactly
+                    float t;
+                    two_sum(S, p, S, t);
+                    E += t + pe;
+                    E = fmaf(a, zl[l], E);
+                    E = fmaf(gl[l], b, E);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const float S2 = __shfl_xor_sync(0xffffffffu, S, o);
+                const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
+                float t;
+                two_sum(S, S2, S, t);
+                E += E2 + t;
+            }
+            if (q == 0 && c < C) {
+                float rh, t;
+                two_sum(wh[c], -S, rh, t);
+                rf[c] = rh + ((wl[c] - E) + t);
+            }
         }
         __syncthreads();
     }
@@ -458,9 +411,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_inv_kernel(
     for (int c = tid; c < C; c += SOLVE_THREADS) {
         const int be = c / Rn, al = c % Rn;
         const int64_t o = ((int64_t)al * In + i) * Rn1 + be;
-        Zn[o] = z[c];
-        if (Znf) Znf[o] = (float)z[c];
-        zw += z[c] * w[c];
+        const double zd = (double)zh[c] + (double)zl[c];
+        Zn[o] = zd;
+        if (Znf) Znf[o] = zh[c] + zl[c];
+        zw += zd * ((double)wh[c] + (double)wl[c]);
     }
     zw = rtr::block_sum(zw, red);
     if (tid == 0) zw_out[i] = zw;
@@ -692,15 +646,15 @@ inline unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 65535) {
 // start+count-1 (indices mod N); writes the product slices for every
 // multi-index (row-major) as rows x Rfirst x Rlast into one of two buffers,
 // returns the buffer holding the result.  final_tr permutes rows as above.
-template <typename T>
-T* build_chain(int N, const int64_t* dims, const int* R, const double* const* Z, int start, int count,
+template <typename T, typename TZ = double>
+T* build_chain(int N, const int64_t* dims, const int* R, const TZ* const* Z, int start, int count,
                T* buf0, T* buf1, int final_tr, int64_t Aa, int64_t Bb, cudaStream_t s, int* status) {
     T* cur = nullptr;
     T* bufs[2] = {buf0, buf1};
     int which = 0;
     int64_t Jp = 1;
     const int Rfirst = R[start % N];
-    const double* zfirst = nullptr;
+    const TZ* zfirst = nullptr;
     int t0 = 0;
     if (count >= 2) {          // fold the first core into the first product
         zfirst = Z[start % N];
@@ -714,8 +668,14 @@ T* build_chain(int N, const int64_t* dims, const int* R, const double* const* Z,
         T* out = bufs[which];
         const int fin = (t == count - 1) ? final_tr : 0;
         const int64_t total = Jp * Km * Rfirst * Rd;
-        subchain_step_kernel<T><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out, fin, Aa, Bb,
-                                                                t == t0 ? zfirst : nullptr);
+        // 32-bit decode when the output (and so every index) stays below 2^31
+        const int64_t outsz = std::max<int64_t>(total, Aa * Bb * Rfirst * Rd);
+        if (outsz < ((int64_t)1 << 31))
+            subchain_step_kernel<T, TZ, uint32_t><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out,
+                                                                              fin, Aa, Bb, t == t0 ? zfirst : nullptr);
+        else
+            subchain_step_kernel<T, TZ, int64_t><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out,
+                                                                             fin, Aa, Bb, t == t0 ? zfirst : nullptr);
         rtr_count_launch();
         if (cudaGetLastError() != cudaSuccess) { *status = RTR_ECUDA; return nullptr; }
         cur = out;
@@ -747,7 +707,8 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     // Mp[1] serves the start's transfer products only; during the sweeps it
     // holds the float32 inverse of the current Gram matrix
     float* Ginv = reinterpret_cast<float*>(Mp[1]);
-    float* Gf = Ginv + 160 * 160;                    // float32 copy of the Gram matrix
+    float* Gf = Ginv + 160 * 160;                    // float32 copy of the Gram matrix (hi part)
+    float* Gfl = Gf + 160 * 160;                     // and its low part
     double* W = ws + (RTR_MAXN + 2) * ESZ;
     double* Wz = W + p->als_wmax;
     double* jac = Wz + p->als_wmax;              // 2 * 144^2 for the pinv fallback
@@ -765,7 +726,7 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
 
     auto transfer = [&](int m) -> int {
         const int Ra = p->R[m], Rb = p->R[(m + 1) % N];
-        transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb), 256, 0, s>>>(Z[m], Ra, (int)Kd[m], Rb, E[m]);
+        transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb, 64), 64, 0, s>>>(Z[m], Ra, (int)Kd[m], Rb, E[m]);
         RTR_LAUNCH_CHECK("transfer_kernel");
         return RTR_OK;
     };
@@ -837,8 +798,6 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
                                       (int)(sizeof(float) * (size_t)cmax * cmax)));
         RTR_CUDA(cudaFuncSetAttribute(als_solve_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * (size_t)cmax * (cmax + 1))));
-        RTR_CUDA(cudaFuncSetAttribute(als_subchain_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      227 * 1024));
     }
     for (int sweep = 0; sweep < p->params.sweeps; ++sweep) {
         for (int n = 0; n < N; ++n) {
@@ -852,48 +811,32 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             if (sweep > 0 || n > 0) {
                 const int m = (n + N - 1) % N;
                 const int Ra = p->R[m], Rb = p->R[(m + 1) % N];
-                transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb), 256, 0, side>>>(Z[m], Ra, (int)Kd[m], Rb, E[m]);
+                // 64-thread blocks: the float64 work spreads over every SM
+                transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb, 64), 64, 0, side>>>(Z[m], Ra, (int)Kd[m], Rb, E[m]);
                 RTR_LAUNCH_CHECK("transfer_kernel");
             }
             GramChainArgs gc{};
             for (int m = 0; m < N; ++m) { gc.E[m] = E[m]; gc.R[m] = p->R[m]; }
             gc.N = N; gc.start = n + 1; gc.cnt = N - 1; gc.out = Mp[0];
-            gc.reindex = 1; gc.Rb = Rn1; gc.Rn = Rn; gc.outf = Gf;
+            gc.reindex = 1; gc.Rb = Rn1; gc.Rn = Rn; gc.outf = Gf; gc.outl = Gfl;
             gram_chain_kernel<<<(unsigned)(Rn1 * Rn1), GC_THREADS, 0, side>>>(gc);
             RTR_LAUNCH_CHECK("gram_chain_kernel");
             if ((st = launch_gram_inverse(Gf, C, Ginv, need_slow, side))) return st;
             RTR_CUDA(cudaEventRecord(p->ev[1], side));
             // ---- caller's stream: W = P_<n> S, subchain generated in the contraction
             // ---- caller's stream: subchain S (natural row order), then W = P_<n> S
-            AlsChainArgs ca{};
-            ca.N = N; ca.n = n;
-            for (int m = 0; m < N; ++m) { ca.Z[m] = Zt[m]; ca.K[m] = Kd[m]; ca.R[m] = p->R[m]; }
-            for (int m = 0; m < N; ++m) {
-                if (m == n) { ca.nstride[m] = 0; continue; }
-                int64_t ns = (m > n) ? 1 : B;
-                for (int m2 = m + 1; m2 < N; ++m2)
-                    if (m2 != n && (m > n || m2 < n)) ns *= Kd[m2];
-                ca.nstride[m] = ns;
-            }
-            for (int t = 0; t < N; ++t) ca.cyc[t] = (n + t) % N;
-            ca.Jpre = 1;
-            for (int t = 1; t <= N - 2; ++t) ca.Jpre *= Kd[ca.cyc[t]];
             if ((size_t)(A * B) * (size_t)C * sizeof(T) > p->sub_bytes)
                 return rtr_set_error(RTR_ENOMEM, "TR-ALS: subchain exceeds the plan workspace");
-            ca.S = p->sub_ws[0];
-            size_t csmem = sizeof(T) * 2 * (size_t)Rn1 * RTR_MAX_RANK;
-            for (int t = 1; t < N; ++t) {
-                const int m = (n + t) % N;
-                csmem += sizeof(T) * (size_t)p->R[m] * Kd[m] * p->R[(m + 1) % N];
-            }
-            if (csmem > 227 * 1024) return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: cores exceed shared memory");
-            const int64_t gx = std::min<int64_t>(ca.Jpre, 2 * (int64_t)p->num_sms);
-            als_subchain_kernel<T><<<(unsigned)gx, 256, csmem, s>>>(ca);
-            RTR_LAUNCH_CHECK("als_subchain_kernel");
+            const T* Zc[RTR_MAXN];
+            for (int m = 0; m < N; ++m) Zc[m] = reinterpret_cast<const T*>(Zt[m]);
+            int cst = RTR_OK;
+            const T* Sn = build_chain<T, T>(N, Kd, p->R, Zc, n + 1, N - 1, reinterpret_cast<T*>(p->sub_ws[0]),
+                                            reinterpret_cast<T*>(p->sub_ws[1]), 1, A, B, s, &cst);
+            if (cst) return rtr_set_error(cst, "TR-ALS: subchain launch failed");
             {
                 ContractArgs w{};
                 w.X = P; w.A = A; w.I = I; w.B = B; w.C = C;
-                w.gen = 0; w.M = p->sub_ws[0]; w.ldm = C;
+                w.gen = 0; w.M = Sn; w.ldm = C;
                 w.Y = W; w.norm_out = nullptr;
                 if ((st = launch_contract(p, is_f64, w, s))) return st;
             }
@@ -903,11 +846,11 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             // refinement: float64 accuracy for FP64 plans; for the float32 / BF16
             // plans one float64-residual correction after the float32 solve
             // (relative error ~(kappa 2^-24)^2)
-            const double tol2 = is_f64 ? 1e-28 : 1e-18;
+            const float tol2 = is_f64 ? 1e-28f : 1e-18f;
             const int max_it = is_f64 ? 12 : 2;
             const size_t gsmem = sizeof(float) * (size_t)C * C;
-            als_solve_inv_kernel<<<(unsigned)I, SOLVE_THREADS, gsmem, s>>>(G, Ginv, Rn, Rn1, (int)I, W, Z[n], Zf[n],
-                                                                          zw, need_slow, tol2, max_it);
+            als_solve_inv_kernel<<<(unsigned)I, SOLVE_THREADS, gsmem, s>>>(Gf, Gfl, Ginv, Rn, Rn1, (int)I, W, Z[n],
+                                                                          Zf[n], zw, need_slow, tol2, max_it);
             RTR_LAUNCH_CHECK("als_solve_inv_kernel");
             const size_t ssmem = sizeof(double) * (size_t)C * (C + 1);
             als_solve_slow_kernel<<<1, 512, ssmem, s>>>(G, Rn, Rn1, (int)I, W, Wz, Z[n], Zf[n], zw, jac,

@@ -45,6 +45,11 @@ __global__ void __launch_bounds__(NT) contract_kernel(
     double nsum = 0.0;
     const int ncalls = (C + 19) / 20;
 
+    // chunk ch = a * nbc + bi, advanced by gridDim.x without 64-bit divisions
+    // (a 64-bit division is a long instruction sequence per chunk)
+    int64_t ca = 0, cb = 0;
+    const int64_t qa = gridDim.x / nbc, qb = gridDim.x % nbc;
+    if (B != 1) { ca = blockIdx.x / nbc; cb = blockIdx.x % nbc; }
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         int64_t a0, b0;
         int len;
@@ -52,8 +57,10 @@ __global__ void __launch_bounds__(NT) contract_kernel(
             a0 = ch * RC; b0 = 0;
             len = (int)min((int64_t)RC, A - a0);
         } else {
-            a0 = ch / nbc; b0 = (ch % nbc) * RC;
+            a0 = ca; b0 = cb * RC;
             len = (int)min((int64_t)RC, B - b0);
+            cb += qb; ca += qa;
+            if (cb >= nbc) { cb -= nbc; ++ca; }
         }
         const int64_t rbase = (B == 1) ? a0 : a0 * B + b0;   // r of rr = 0
         __syncthreads();
@@ -198,7 +205,7 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
     int64_t gx = std::max<int64_t>(1, (int64_t)occ * p->num_sms / sh.gy);
     // a stored operand (the TR-ALS contraction) is small: give every CTA a few
     // chunks so that the partial reduction stays short
-    if (!GEN) gx = std::min<int64_t>(gx, std::max<int64_t>(1, nchunks / 4));
+    if (!GEN) gx = std::min<int64_t>(gx, std::max<int64_t>(1, nchunks / 2));
     gx = std::min<int64_t>(gx, nchunks);
     gx = std::max<int64_t>(gx, 1);
     const int64_t need = gx * a.I * a.C;

@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
                                                  int NKT, int CT, int IC, int64_t ntiles, int64_t nbt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int KP = NKT * TKO;
-    const int xld = CT + 1;
+    // X tile row pitch: odd for the scalar variants (conflict-free transposed
+    // stores), a multiple of 4 for the 4-wide variants (16-byte vector loads)
+    const int xld = (TC % 4 == 0) ? CT + 4 : CT + 1;
     T* Qs = reinterpret_cast<T*>(smem_raw);     // [IC][KP]
     T* Xs = Qs + (size_t)IC * KP;              // [IC][xld]
     int* cmap = reinterpret_cast<int*>(Xs + (size_t)IC * xld);   // [CT] (a << 16) | b, short fibres
@@ -87,10 +89,20 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const T* __restrict__ X, int64_
 #pragma unroll 4
             for (int il = 0; il < ic; ++il) {
                 T qv[TKO], xv[TC];
+                if constexpr (sizeof(T) == 4 && TKO % 4 == 0 && TC % 4 == 0) {
+                    // 16-byte shared loads: KP and xld are multiples of 4 floats
 #pragma unroll
-                for (int o = 0; o < TKO; ++o) qv[o] = Qs[il * KP + tko * TKO + o];
+                    for (int o = 0; o < TKO; o += 4)
+                        *reinterpret_cast<float4*>(&qv[o]) = *reinterpret_cast<const float4*>(&Qs[il * KP + tko * TKO + o]);
 #pragma unroll
-                for (int c = 0; c < TC; ++c) xv[c] = Xs[il * xld + tc * TC + c];
+                    for (int c = 0; c < TC; c += 4)
+                        *reinterpret_cast<float4*>(&xv[c]) = *reinterpret_cast<const float4*>(&Xs[il * xld + tc * TC + c]);
+                } else {
+#pragma unroll
+                    for (int o = 0; o < TKO; ++o) qv[o] = Qs[il * KP + tko * TKO + o];
+#pragma unroll
+                    for (int c = 0; c < TC; ++c) xv[c] = Xs[il * xld + tc * TC + c];
+                }
 #pragma unroll
                 for (int o = 0; o < TKO; ++o)
 #pragma unroll
@@ -124,9 +136,10 @@ int launch_variant(rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B, con
     if (CT < TC) return rtr_set_error(RTR_EINVAL, "mode product tile does not fit");
     // I chunk: at most 128 (float64) / 256 (float32) rows, and the staged Q
     // and X chunks within 100 KB so that two CTAs fit on an SM
-    const int64_t fit = (int64_t)(100 * 1024) / (int64_t)(sizeof(T) * (nkt * TKO + CT + 1));
+    const int xld = (TC % 4 == 0) ? CT + 4 : CT + 1;
+    const int64_t fit = (int64_t)(100 * 1024) / (int64_t)(sizeof(T) * (nkt * TKO + xld));
     const int IC = (int)std::max<int64_t>(1, std::min<int64_t>({I, sizeof(T) == 8 ? 128 : 256, fit}));
-    const size_t smem = sizeof(T) * ((size_t)IC * nkt * TKO + (size_t)IC * (CT + 1)) + sizeof(int) * (size_t)CT;
+    const size_t smem = sizeof(T) * ((size_t)IC * nkt * TKO + (size_t)IC * xld) + sizeof(int) * (size_t)CT;
     int64_t ntiles, nbt = 1;
     if (B == 1) ntiles = rtr_ceil_div(A, CT);
     else if (B < CT) ntiles = rtr_ceil_div(A, CT / B);      // whole a-blocks per tile
@@ -148,10 +161,11 @@ int run_variant(int v, rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B,
         case 0: return launch_variant<T, 4, 2>(p, X, A, I, B, Q, K, out, s);
         case 1: return launch_variant<T, 2, 4>(p, X, A, I, B, Q, K, out, s);
         case 2: return launch_variant<T, 4, 4>(p, X, A, I, B, Q, K, out, s);
-        default: return launch_variant<T, 8, 2>(p, X, A, I, B, Q, K, out, s);
+        case 3: return launch_variant<T, 8, 2>(p, X, A, I, B, Q, K, out, s);
+        default: return launch_variant<T, 8, 4>(p, X, A, I, B, Q, K, out, s);
     }
 }
-constexpr int NVARIANTS = 4;
+constexpr int NVARIANTS = 5;
 
 // Autotuner: the first product of a shape class (type, I, K, layout of B)
 // outside stream capture times every tile variant on the call's own data
