@@ -84,33 +84,42 @@ __device__ inline double block_sum(double v, double* red /* >= 32 doubles */) {
 }
 
 // Cyclic Jacobi eigendecomposition of a symmetric n x n matrix A (row-major,
-// ld) in shared memory, parallel round-robin pairing (n/2 disjoint rotations
-// per step).  On return the diagonal of A holds the eigenvalues and the
-// columns of V (n x n, ld) the eigenvectors.  `pairs` needs 2*((n+1)/2) ints,
-// `cs` needs 2*((n+1)/2) doubles.
-__device__ inline void block_jacobi_eig(double* A, double* V, int n, int ld, int* pairs, double* cs,
-                                        int max_sweeps) {
+// ld) in memory visible to the block, parallel round-robin pairing (n/2
+// disjoint rotations per step), in the arithmetic type T.  On return the
+// diagonal of A holds the eigenvalues and the columns of V (n x n, ld) the
+// eigenvectors.  `pairs` needs 2*((n+1)/2) ints, `cs` needs 2*((n+1)/2) T.
+// A sweep ends the iteration once the off-diagonal mass is at most
+// off_tol times the total (block-wide reduction, every thread takes part).
+template <typename T>
+__device__ inline void block_jacobi_eig(T* A, T* V, int n, int ld, int* pairs, T* cs, int max_sweeps,
+                                        T off_tol) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
+    for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? T(1) : T(0);
     __syncthreads();
     if (n < 2) return;
     const int m = (n + 1) & ~1;             // even player count (dummy = n when odd)
     const int np = m / 2;
-    __shared__ double off_s, tot_s;
+    __shared__ T red_off[32], red_tot[32];
+    const int lane = tid & 31, w = tid >> 5, nw = (nt + 31) >> 5;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         // convergence test: off-diagonal mass relative to the whole
-        if (tid == 0) {
-            double off = 0.0, tot = 0.0;
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) {
-                    const double a = A[i * ld + j];
-                    tot += a * a;
-                    if (i != j) off += a * a;
-                }
-            off_s = off; tot_s = tot;
+        T off = T(0), tot = T(0);
+        for (int e = tid; e < n * n; e += nt) {
+            const int i = e / n, j = e % n;
+            const T a = A[i * ld + j];
+            tot += a * a;
+            if (i != j) off += a * a;
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (lane == 0) { red_off[w] = off; red_tot[w] = tot; }
         __syncthreads();
-        if (!(off_s > 1e-30 * tot_s)) break;
+        off = T(0); tot = T(0);
+        for (int u = 0; u < nw; ++u) { off += red_off[u]; tot += red_tot[u]; }
+        __syncthreads();
+        if (!(off > off_tol * tot)) break;
         for (int step = 0; step < m - 1; ++step) {
             // round-robin pairing: player 0 fixed, others rotate
             for (int k = tid; k < np; k += nt) {
@@ -118,14 +127,14 @@ __device__ inline void block_jacobi_eig(double* A, double* V, int n, int ld, int
                 int q = 1 + (m - 2 - k + step) % (m - 1);
                 if (p > q) { const int t = p; p = q; q = t; }
                 pairs[2 * k] = p; pairs[2 * k + 1] = q;
-                double c = 1.0, sn = 0.0;
+                T c = T(1), sn = T(0);
                 if (q < n) {
-                    const double apq = A[p * ld + q];
-                    if (apq != 0.0) {
-                        const double app = A[p * ld + p], aqq = A[q * ld + q];
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    const T apq = A[p * ld + q];
+                    if (apq != T(0)) {
+                        const T app = A[p * ld + p], aqq = A[q * ld + q];
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                        c = T(1) / sqrt(T(1) + t * t);
                         sn = t * c;
                     }
                 }
@@ -137,8 +146,8 @@ __device__ inline void block_jacobi_eig(double* A, double* V, int n, int ld, int
                 const int k = e / n, j = e % n;
                 const int p = pairs[2 * k], q = pairs[2 * k + 1];
                 if (q >= n) continue;
-                const double c = cs[2 * k], sn = cs[2 * k + 1];
-                const double ap = A[p * ld + j], aq = A[q * ld + j];
+                const T c = cs[2 * k], sn = cs[2 * k + 1];
+                const T ap = A[p * ld + j], aq = A[q * ld + j];
                 A[p * ld + j] = c * ap - sn * aq;
                 A[q * ld + j] = sn * ap + c * aq;
             }
@@ -148,11 +157,11 @@ __device__ inline void block_jacobi_eig(double* A, double* V, int n, int ld, int
                 const int k = e / n, i = e % n;
                 const int p = pairs[2 * k], q = pairs[2 * k + 1];
                 if (q >= n) continue;
-                const double c = cs[2 * k], sn = cs[2 * k + 1];
-                const double ap = A[i * ld + p], aq = A[i * ld + q];
+                const T c = cs[2 * k], sn = cs[2 * k + 1];
+                const T ap = A[i * ld + p], aq = A[i * ld + q];
                 A[i * ld + p] = c * ap - sn * aq;
                 A[i * ld + q] = sn * ap + c * aq;
-                const double vp = V[i * ld + p], vq = V[i * ld + q];
+                const T vp = V[i * ld + p], vq = V[i * ld + q];
                 V[i * ld + p] = c * vp - sn * vq;
                 V[i * ld + q] = sn * vp + c * vq;
             }

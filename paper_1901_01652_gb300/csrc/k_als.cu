@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __res
         __shared__ double cs[2 * 160];
         for (int e = threadIdx.x; e < C * C; e += blockDim.x) Aj[e] = Mprod[e];
         __syncthreads();
-        rtr::block_jacobi_eig(Aj, V, C, C, pairs, cs, 40);
+        rtr::block_jacobi_eig<double>(Aj, V, C, C, pairs, cs, 40, 1e-30);
         double lmax = 0.0;
         for (int c = 0; c < C; ++c) lmax = fmax(lmax, Aj[c * C + c]);
         const double cut = 1e-13 * lmax;

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) features_kernel(const FeatArgs p) {
         A[b * K + a] = s;
     }
     __syncthreads();
-    rtr::block_jacobi_eig(A, V, K, K, pairs, cs, 40);
+    rtr::block_jacobi_eig<double>(A, V, K, K, pairs, cs, 40, 1e-30);
     __syncthreads();
     for (int i = tid; i < K; i += blockDim.x) lam[i] = A[i * K + i];
     __syncthreads();

@@ -23,50 +23,65 @@ inline unsigned gridn(int64_t n, int t = 256) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
 }
 
-// G = C C^T (left) or C^T C (right), m x m float64, one output per thread.
+// G = C C^T (left) or C^T C (right), m x m float64: one warp per output
+// (i <= j), lanes split the long sum (every SM takes part: float64 work is
+// slow on this GPU, so it is spread as widely as possible).
 template <typename T>
 __global__ void gram_kernel(const T* __restrict__ Cm, int64_t rows, int64_t cols, int left, double* __restrict__ G) {
     const int64_t m = left ? rows : cols;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = left ? cols : rows;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m * m; e += nw) {
         const int64_t i = e / m, j = e % m;
-        if (j < i) continue;
+        if (j < i) continue;                           // uniform per warp
         double s = 0.0;
         if (left)
-            for (int64_t l = 0; l < cols; ++l) s += (double)Cm[i * cols + l] * (double)Cm[j * cols + l];
+            for (int64_t l = lane; l < len; l += 32) s += (double)Cm[i * cols + l] * (double)Cm[j * cols + l];
         else
-            for (int64_t l = 0; l < rows; ++l) s += (double)Cm[l * cols + i] * (double)Cm[l * cols + j];
-        G[i * m + j] = s;
-        G[j * m + i] = s;
+            for (int64_t l = lane; l < len; l += 32) s += (double)Cm[l * cols + i] * (double)Cm[l * cols + j];
+        s = rtr::warp_sum(s);
+        if (lane == 0) {
+            G[i * m + j] = s;
+            G[j * m + i] = s;
+        }
     }
 }
 
-// Jacobi eigendecomposition of G (m x m, global memory) in one CTA; then sort
-// eigenpairs by decreasing eigenvalue into lam[m] and Vs (m x m, columns).
-__global__ void __launch_bounds__(1024) eig_kernel(double* __restrict__ G, double* __restrict__ V, int m,
+// Jacobi eigendecomposition of G (m x m, global memory) in one CTA, in the
+// arithmetic type T (float64 for FP64 plans; float32 for the float plans,
+// whose decomposition input P is float32 anyway: float64 rotations on this
+// GPU cost about a hundred times more); then sort eigenpairs by decreasing
+// eigenvalue into lam[m] and Vs (m x m, columns), both float64.
+template <typename T>
+__global__ void __launch_bounds__(1024) eig_kernel(double* __restrict__ G, T* __restrict__ A, T* __restrict__ V, int m,
                                                    double* __restrict__ lam, double* __restrict__ Vs,
                                                    int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = (m + 1) / 2 + 1;
-    double* cs = reinterpret_cast<double*>(smem_raw);            // 2 np
+    T* cs = reinterpret_cast<T*>(smem_raw);                      // 2 np
     int* pairs = reinterpret_cast<int*>(cs + 2 * np);            // 2 np
-    rtr::block_jacobi_eig(G, V, m, m, pairs, cs, 60);
+    if ((void*)A != (void*)G)
+        for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) A[e] = (T)G[e];
+    __syncthreads();
+    rtr::block_jacobi_eig<T>(A, V, m, m, pairs, cs, 60, sizeof(T) == 8 ? T(1e-30) : T(1e-13));
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < m; ++i) order[i] = i;
         // insertion sort by decreasing eigenvalue (m is small)
         for (int i = 1; i < m; ++i) {
             const int o = order[i];
-            const double v = G[(int64_t)o * m + o];
+            const T v = A[(int64_t)o * m + o];
             int j = i - 1;
-            while (j >= 0 && G[(int64_t)order[j] * m + order[j]] < v) { order[j + 1] = order[j]; --j; }
+            while (j >= 0 && A[(int64_t)order[j] * m + order[j]] < v) { order[j + 1] = order[j]; --j; }
             order[j + 1] = o;
         }
-        for (int i = 0; i < m; ++i) lam[i] = G[(int64_t)order[i] * m + order[i]];
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = (double)A[(int64_t)order[i] * m + order[i]];
     for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
         const int64_t r = e / m, c = e % m;
-        Vs[e] = V[r * m + order[c]];
+        Vs[e] = (double)V[r * m + order[c]];
     }
 }
 
@@ -158,16 +173,25 @@ struct SvdWs {
 
 // one truncated SVD of C (rows x cols); returns rank (host), writes U (rows x r)
 // and the carry (r x cols) into ws
+// eig32: eigendecomposition in float32 (the float plans) instead of float64
 template <typename T>
 int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, int cap, SvdWs& w, int* r_out,
-             int* overflow, cudaStream_t s) {
+             int* overflow, bool eig32, cudaStream_t s) {
     const int left = rows <= cols;
     const int m = (int)(left ? rows : cols);
-    gram_kernel<T><<<gridn((int64_t)m * m), 256, 0, s>>>(Cm, rows, cols, left, w.G);
+    gram_kernel<T><<<gridn((int64_t)m * m * 32), 256, 0, s>>>(Cm, rows, cols, left, w.G);
     RTR_LAUNCH_CHECK("gram_kernel");
     const size_t np = (size_t)(m + 1) / 2 + 1;
-    const size_t smem = 2 * np * (sizeof(double) + sizeof(int));
-    eig_kernel<<<1, 1024, smem, s>>>(w.G, w.V, m, w.lam, w.Vs, w.iv + 2);
+    if (!eig32) {
+        const size_t smem = 2 * np * (sizeof(double) + sizeof(int));
+        eig_kernel<double><<<1, 1024, smem, s>>>(w.G, w.G, w.V, m, w.lam, w.Vs, w.iv + 2);
+    } else {
+        // float32 working copies in the (float64-sized) V buffer
+        float* A32 = reinterpret_cast<float*>(w.V);
+        float* V32 = A32 + (size_t)m * m;
+        const size_t smem = 2 * np * (sizeof(float) + sizeof(int));
+        eig_kernel<float><<<1, 1024, smem, s>>>(w.G, A32, V32, m, w.lam, w.Vs, w.iv + 2);
+    }
     RTR_LAUNCH_CHECK("eig_kernel");
     int r = forced;
     if (forced <= 0) {
@@ -180,7 +204,8 @@ int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, in
         *overflow |= h[1];
     }
     if (r < 1 || r > m) return rtr_set_error(RTR_EINVAL, "TR-SVD rank %d outside [1, %d]", r, m);
-    left_vectors_kernel<T><<<gridn(rows * r), 256, 0, s>>>(Cm, rows, cols, left, w.Vs, w.lam, m, r, w.U);
+    // 64-thread blocks: the float64 dot products spread over every SM
+    left_vectors_kernel<T><<<gridn(rows * r, 64), 64, 0, s>>>(Cm, rows, cols, left, w.Vs, w.lam, m, r, w.U);
     RTR_LAUNCH_CHECK("left_vectors_kernel");
     *r_out = r;
     return RTR_OK;
@@ -216,8 +241,9 @@ int trsvd_impl(rtr_plan* p, const T* P, double tol, double* const* Z, int* ranks
     int64_t rest = p->pnumel / K[0];
     int cap0 = p->R[0] * p->R[1];
     int r = 0;
+    const bool eig32 = p->params.prec != RTR_FP64;
     int st = svd_step<T>(P, K[0], rest, std::sqrt(2.0) * delta, forced ? ranks[0] * ranks[1] : 0, cap0, w, &r,
-                         &overflow, s);
+                         &overflow, eig32, s);
     if (st) return st;
     int R0, R1;
     if (forced) { R0 = ranks[0]; R1 = ranks[1]; }
@@ -236,7 +262,7 @@ int trsvd_impl(rtr_plan* p, const T* P, double tol, double* const* Z, int* ranks
     R[0] = R0; R[1] = R1;
     core0_kernel<<<gridn((int64_t)K[0] * r), 256, 0, s>>>(w.U, (int)K[0], R0, R1, Z[0]);
     RTR_LAUNCH_CHECK("core0_kernel");
-    carry_kernel<T><<<gridn((int64_t)r * rest), 256, 0, s>>>(P, K[0], rest, w.U, r, w.Cbuf1);
+    carry_kernel<T><<<gridn((int64_t)r * rest, 64), 64, 0, s>>>(P, K[0], rest, w.U, r, w.Cbuf1);
     RTR_LAUNCH_CHECK("carry_kernel");
     permute_first_kernel<<<gridn((int64_t)r * rest), 256, 0, s>>>(w.Cbuf1, R0, R1, rest, w.Cbuf0);
     RTR_LAUNCH_CHECK("permute_first_kernel");
@@ -248,13 +274,13 @@ int trsvd_impl(rtr_plan* p, const T* P, double tol, double* const* Z, int* ranks
         const int64_t cols = (int64_t)r * rest / rows;       // total stays r * rest
         int rk = 0;
         const int cap = p->R[k + 1];
-        st = svd_step<double>(Ccur, rows, cols, delta, forced ? ranks[k + 1] : 0, cap, w, &rk, &overflow, s);
+        st = svd_step<double>(Ccur, rows, cols, delta, forced ? ranks[k + 1] : 0, cap, w, &rk, &overflow, eig32, s);
         if (st) return st;
         R[k + 1] = rk;
         // core k = U reshaped (R_k, K_k, R_{k+1})
         copy_kernel<<<gridn(rows * rk), 256, 0, s>>>(w.U, rows * rk, Z[k]);
         RTR_LAUNCH_CHECK("copy_kernel");
-        carry_kernel<double><<<gridn((int64_t)rk * cols), 256, 0, s>>>(Ccur, rows, cols, w.U, rk, Cnext);
+        carry_kernel<double><<<gridn((int64_t)rk * cols, 64), 64, 0, s>>>(Ccur, rows, cols, w.U, rk, Cnext);
         RTR_LAUNCH_CHECK("carry_kernel");
         std::swap(Ccur, Cnext);
         r = rk;

@@ -86,9 +86,13 @@ def test_trsvd_forced_ranks_and_fp32():
 
 
 def test_trsvd_exact_recovery_small_rank():
+    # The GPU reads singular values from float64 Gram matrices, whose rounding
+    # leaves eigenvalues of about u ||P||^2 in the null space; the rank test
+    # compares the eigenvalue tail with (eps ||P||)^2 / N, so eps must sit well
+    # above sqrt(u) ~ 1e-8 for the exact rank to be found.
     dims, R = (9, 8, 7), (2, 2, 2)
     P = ot.tr_full(workloads.tr_cores(dims, R, 42))
-    Zg, rg = gpu_trsvd(P, 1e-9, "fp64", [8, 8, 8])
+    Zg, rg = gpu_trsvd(P, 1e-6, "fp64", [8, 8, 8])
     assert rg[0] * rg[1] == 4
     assert rel(ot.tr_full(Zg), P) < 1e-9
 
