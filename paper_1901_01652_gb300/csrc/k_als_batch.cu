@@ -29,7 +29,7 @@ namespace {
 
 constexpr int CT_THREADS = 256;
 constexpr int SV_THREADS = 512;
-constexpr int LB = 16;              // last-mode indices per contraction block
+constexpr int LB = 32;              // last-mode indices per contraction block (K_n <= 64: at most 2)
 constexpr int MAXC = 160;           // C = R_n R_{n+1} <= 144
 
 template <typename T>
@@ -141,6 +141,135 @@ __global__ void __launch_bounds__(CT_THREADS) bgram_kernel(const BTensor<T>* __r
 }
 
 // ---- W = P_<n> S: items of subchain prefixes --------------------------------
+// One work item (tensor, prefix range) of the batched contraction, with the
+// register tile depth IP (i values per thread) fixed at compile time: the
+// accumulation loop then carries no per-k predicates.  Thread mappings are
+// computed once per item (no integer divisions inside the prefix loop).
+template <typename T, int IP>
+__device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, double* __restrict__ partial,
+                                               const int* sK, const int* sR, const int* scyc, const int64_t* sstride,
+                                               const T* const* Zc, const T* __restrict__ Pt, T* M0, T* M1, T* S,
+                                               T* Pv, const rtr::WTile& wt) {
+    const int tid = threadIdx.x;
+    const int ml = scyc[N - 1];
+    const int Rb = sR[(n + 1) % N], Rn = sR[n];
+    const int C = Rb * Rn;
+    const int Cp = rtr::tile_cp(C);
+    const int Kn = sK[n];
+    const int Kl = sK[ml];
+    const int Rl = sR[ml];
+    const int64_t str_n = sstride[n], str_l = sstride[ml];
+    // S rows: thread -> column c (fixed), rows l = l_s, l_s + s_pass, ...
+    const int s_pass = max(1, CT_THREADS / Cp);
+    const int sc = tid % Cp, l_s = tid / Cp;
+    const bool s_on = l_s < s_pass;
+    const int s_be = (sc < C) ? sc / Rn : 0, s_al = (sc < C) ? sc % Rn : 0;
+    // P rows: thread -> i (fixed), rows l = l_p, l_p + p_pass, ...
+    const int p_pass = max(1, CT_THREADS / Kn);
+    const int pi = tid % Kn, l_p = tid / Kn;
+    const bool p_on = l_p < p_pass;
+    const int zst = Kl * Rn;
+    T acc[IP][4];
+#pragma unroll
+    for (int k = 0; k < IP; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[k][j] = T(0);
+    for (int64_t jp = ci.jp0; jp < ci.jp1; ++jp) {
+        // prefix decode in 32 bits (a 64-bit division is a long sequence)
+        uint32_t rem = (uint32_t)jp;
+        int64_t base = 0;
+        int idx[RTR_MAXN];
+        for (int t = N - 2; t >= 1; --t) {
+            const int m = scyc[t];
+            const uint32_t km = (uint32_t)sK[m];
+            idx[t] = (int)(rem % km);
+            rem /= km;
+            base += idx[t] * sstride[m];
+        }
+        __syncthreads();
+        {
+            const int m = scyc[1];
+            const int Rc = sR[(m + 1) % N];
+            const int Km = sK[m];
+            for (int e = tid; e < Rb * Rc; e += blockDim.x) {
+                const int be = e / Rc, gg = e % Rc;
+                M0[be * RTR_MAX_RANK + gg] = Zc[m][(be * Km + idx[1]) * Rc + gg];
+            }
+        }
+        T* cur = M0;
+        T* nxt = M1;
+        for (int t = 2; t <= N - 2; ++t) {
+            __syncthreads();
+            const int m = scyc[t];
+            const int Rm = sR[m], Rc = sR[(m + 1) % N], Km = sK[m];
+            const T* zm = Zc[m] + idx[t] * Rc;
+            for (int e = tid; e < Rb * Rc; e += blockDim.x) {
+                const int be = e / Rc, gg = e % Rc;
+                T sum = T(0);
+                for (int c = 0; c < Rm; ++c) sum = dfma(cur[be * RTR_MAX_RANK + c], zm[c * Km * Rc + gg], sum);
+                nxt[be * RTR_MAX_RANK + gg] = sum;
+            }
+            T* tmp = cur; cur = nxt; nxt = tmp;
+        }
+        __syncthreads();
+        for (int l0 = 0; l0 < Kl; l0 += LB) {
+            const int lb = min(LB, Kl - l0);
+            if (s_on) {
+                const T* mrow = cur + s_be * RTR_MAX_RANK;
+                const T* zl = Zc[ml] + l0 * Rn + s_al;
+                for (int l = l_s; l < lb; l += s_pass) {
+                    T sum = T(0);
+                    if (sc < C)
+                        for (int gg = 0; gg < Rl; ++gg) sum = dfma(mrow[gg], zl[gg * zst + l * Rn], sum);
+                    S[l * Cp + sc] = sum;
+                }
+            }
+            if (p_on) {
+                const T* prow = Pt + base + (int64_t)pi * str_n;
+                for (int l = l_p; l < lb; l += p_pass) Pv[l * Kn + pi] = prow[(int64_t)(l0 + l) * str_l];
+            }
+            __syncthreads();
+            if (wt.active) {
+#pragma unroll 2
+                for (int l = 0; l < lb; ++l) {
+                    const T* srow = S + l * Cp + wt.c0;
+                    T sv[4];
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(srow);
+                        sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) sv[j] = srow[j];
+                    }
+                    const T* prw = Pv + l * Kn;
+#pragma unroll
+                    for (int k = 0; k < IP; ++k) {
+                        const int i = wt.ti + wt.Ti * k;
+                        const T pv = (i < Kn) ? prw[i] : T(0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[k][j] = dfma(pv, sv[j], acc[k][j]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (wt.active) {
+        double* out = partial + ci.off;
+#pragma unroll
+        for (int k = 0; k < IP; ++k) {
+            const int i = wt.ti + wt.Ti * k;
+            if (i < Kn) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = wt.c0 + j;
+                    if (c < C) out[(int64_t)i * C + c] = (double)acc[k][j];
+                }
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(CT_THREADS) bcontract_kernel(const BTensor<T>* __restrict__ tens,
                                                                const CItem* __restrict__ items, int nitems, int N,
@@ -151,97 +280,52 @@ __global__ void __launch_bounds__(CT_THREADS) bcontract_kernel(const BTensor<T>*
     T* S = M1 + RTR_MAX_RANK * RTR_MAX_RANK;         // LB x Cp (Cp <= 144)
     T* Pv = S + LB * 144;                            // LB x K_n (K_n <= 64)
     T* Zs0 = Pv + LB * 64;                           // the other cores (if `stage`)
+    // this item's tensor descriptor, cached in shared memory: reading it from
+    // the global BTensor inside the loops would repeat dependent global loads
+    __shared__ int sK[RTR_MAXN], sR[RTR_MAXN], scyc[RTR_MAXN];
+    __shared__ int64_t sstride[RTR_MAXN];
+    __shared__ const T* sZ[RTR_MAXN];
+    __shared__ const T* sP;
     const int tid = threadIdx.x;
-    int cyc[RTR_MAXN];
-    for (int t = 0; t < N; ++t) cyc[t] = (n + t) % N;
-    const int ml = cyc[N - 1];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const CItem ci = items[it];
-        const BTensor<T>& b = tens[ci.t];
-        const int Rb = b.R[(n + 1) % N], Rn = b.R[n];
-        const int C = Rb * Rn;
-        const int Cp = rtr::tile_cp(C);
-        const int Kn = (int)b.K[n];
-        const int Kl = (int)b.K[ml];
-        const int Rl = b.R[ml];
+        __syncthreads();                             // previous item done with the shared state
+        if (tid < N) {
+            const BTensor<T>& b = tens[ci.t];
+            sK[tid] = (int)b.K[tid];
+            sR[tid] = b.R[tid];
+            sstride[tid] = b.stride[tid];
+            scyc[tid] = (n + tid) % N;
+            sZ[tid] = b.Zt[tid];
+            if (tid == 0) sP = b.P;
+        }
+        __syncthreads();
         // the other cores of this tensor, read many times per prefix: staged
         // in shared memory (if they fit) instead of dependent global loads
         const T* Zc[RTR_MAXN];
-        __syncthreads();
         {
             T* zs = Zs0;
             for (int t = 1; t < N; ++t) {
-                const int m = cyc[t];
+                const int m = scyc[t];
                 if (stage) {
-                    const int cnt = b.R[m] * (int)b.K[m] * b.R[(m + 1) % N];
-                    for (int e = tid; e < cnt; e += blockDim.x) zs[e] = b.Zt[m][e];
+                    const int cnt = sR[m] * sK[m] * sR[(m + 1) % N];
+                    for (int e = tid; e < cnt; e += blockDim.x) zs[e] = sZ[m][e];
                     Zc[m] = zs;
                     zs += cnt;
                 } else {
-                    Zc[m] = b.Zt[m];
+                    Zc[m] = sZ[m];
                 }
             }
         }
-        const rtr::WTile wt = rtr::wtile(C, Kn);
-        T acc[rtr::TILE_IP][4];
-        rtr::wtile_zero(acc);
-        for (int64_t jp = ci.jp0; jp < ci.jp1; ++jp) {
-            int64_t rem = jp, base = 0;
-            int idx[RTR_MAXN];
-            for (int t = N - 2; t >= 1; --t) {
-                const int m = cyc[t];
-                idx[t] = (int)(rem % b.K[m]);
-                rem /= b.K[m];
-                base += idx[t] * b.stride[m];
-            }
-            __syncthreads();
-            {
-                const int m = cyc[1];
-                const int Rc = b.R[(m + 1) % N];
-                for (int e = tid; e < Rb * Rc; e += blockDim.x) {
-                    const int be = e / Rc, gg = e % Rc;
-                    M0[be * RTR_MAX_RANK + gg] = Zc[m][((int64_t)be * b.K[m] + idx[1]) * Rc + gg];
-                }
-            }
-            T* cur = M0;
-            T* nxt = M1;
-            for (int t = 2; t <= N - 2; ++t) {
-                __syncthreads();
-                const int m = cyc[t];
-                const int Rm = b.R[m], Rc = b.R[(m + 1) % N];
-                for (int e = tid; e < Rb * Rc; e += blockDim.x) {
-                    const int be = e / Rc, gg = e % Rc;
-                    T sum = T(0);
-                    for (int c = 0; c < Rm; ++c)
-                        sum = dfma(cur[be * RTR_MAX_RANK + c], Zc[m][((int64_t)c * b.K[m] + idx[t]) * Rc + gg], sum);
-                    nxt[be * RTR_MAX_RANK + gg] = sum;
-                }
-                T* tmp = cur; cur = nxt; nxt = tmp;
-            }
-            __syncthreads();
-            for (int l0 = 0; l0 < Kl; l0 += LB) {
-                const int lb = min(LB, Kl - l0);
-                for (int e = tid; e < lb * Cp; e += blockDim.x) {
-                    const int l = e / Cp, c = e % Cp;
-                    T sum = T(0);
-                    if (c < C) {
-                        const int be = c / Rn, al = c % Rn;
-                        const T* zl = Zc[ml] + (int64_t)(l0 + l) * Rn + al;
-                        const int64_t zst = (int64_t)Kl * Rn;
-                        for (int gg = 0; gg < Rl; ++gg) sum = dfma(cur[be * RTR_MAX_RANK + gg], zl[gg * zst], sum);
-                    }
-                    S[e] = sum;
-                }
-                for (int e = tid; e < lb * Kn; e += blockDim.x) {
-                    const int l = e / Kn, i = e % Kn;
-                    Pv[e] = b.P[base + (int64_t)(l0 + l) * b.stride[ml] + (int64_t)i * b.stride[n]];
-                }
-                __syncthreads();
-                rtr::wtile_accum(acc, wt, Pv, Kn, S, Cp, lb);
-                __syncthreads();
-            }
+        const int C = sR[(n + 1) % N] * sR[n];
+        const rtr::WTile wt = rtr::wtile(C, sK[n]);
+        switch (wt.ip) {
+#define RTR_IP_CASE(v) case v: bcontract_item<T, v>(ci, N, n, partial, sK, sR, scyc, sstride, Zc, sP, M0, M1, S, Pv, wt); break;
+            RTR_IP_CASE(1) RTR_IP_CASE(2) RTR_IP_CASE(3) RTR_IP_CASE(4) RTR_IP_CASE(5)
+            RTR_IP_CASE(6) RTR_IP_CASE(7) RTR_IP_CASE(8) RTR_IP_CASE(9)
+            default: bcontract_item<T, rtr::TILE_IP>(ci, N, n, partial, sK, sR, scyc, sstride, Zc, sP, M0, M1, S, Pv, wt); break;
+#undef RTR_IP_CASE
         }
-        rtr::wtile_store(acc, wt, Kn, C, partial + ci.off);
     }
 }
 
