@@ -143,28 +143,36 @@ __global__ void __launch_bounds__(CT_THREADS) bgram_kernel(const BTensor<T>* __r
 // ---- W = P_<n> S: items of subchain prefixes --------------------------------
 // One work item (tensor, prefix range) of the batched contraction, with the
 // register tile depth IP (i values per thread) fixed at compile time: the
-// accumulation loop then carries no per-k predicates.  Thread mappings are
-// computed once per item (no integer divisions inside the prefix loop).
+// accumulation loop then carries no per-k predicates.  A prefix fixes the
+// indices of the cyclic modes c_1 .. c_{N-3} (none when N = 3); its product M
+// (identity when empty) is extended once by every slice of mode c_{N-2}
+// (M2[i2] = M Z_{c_{N-2}}(i2), in shared memory), and the subchain rows
+// (i2, l) then stream through in blocks of LB: far fewer barriers per row
+// than one prefix per (i2).  Thread mappings are computed once per item.
 template <typename T, int IP>
 __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, double* __restrict__ partial,
                                                const int* sK, const int* sR, const int* scyc, const int64_t* sstride,
-                                               const T* const* Zc, const T* __restrict__ Pt, T* M0, T* M1, T* S,
-                                               T* Pv, const rtr::WTile& wt) {
+                                               const T* const* Zc, const T* __restrict__ Pt, T* M0, T* M1, T* M2,
+                                               T* S, T* Pv, const rtr::WTile& wt) {
     const int tid = threadIdx.x;
     const int ml = scyc[N - 1];
+    const int m2 = scyc[N - 2];
     const int Rb = sR[(n + 1) % N], Rn = sR[n];
     const int C = Rb * Rn;
     const int Cp = rtr::tile_cp(C);
     const int Kn = sK[n];
     const int Kl = sK[ml];
-    const int Rl = sR[ml];
-    const int64_t str_n = sstride[n], str_l = sstride[ml];
-    // S rows: thread -> column c (fixed), rows l = l_s, l_s + s_pass, ...
+    const int Rl = sR[ml];                      // right rank of mode c_{N-2} = left rank of the last
+    const int K2 = sK[m2];
+    const int R2 = sR[m2];                      // left rank of mode c_{N-2}
+    const int64_t str_n = sstride[n], str_l = sstride[ml], str_2 = sstride[m2];
+    const int nrows = K2 * Kl;
+    // S rows: thread -> column c (fixed), rows q = l_s, l_s + s_pass, ...
     const int s_pass = max(1, CT_THREADS / Cp);
     const int sc = tid % Cp, l_s = tid / Cp;
     const bool s_on = l_s < s_pass;
     const int s_be = (sc < C) ? sc / Rn : 0, s_al = (sc < C) ? sc % Rn : 0;
-    // P rows: thread -> i (fixed), rows l = l_p, l_p + p_pass, ...
+    // P rows: thread -> i (fixed), rows q = l_p, l_p + p_pass, ...
     const int p_pass = max(1, CT_THREADS / Kn);
     const int pi = tid % Kn, l_p = tid / Kn;
     const bool p_on = l_p < p_pass;
@@ -179,7 +187,7 @@ __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, do
         uint32_t rem = (uint32_t)jp;
         int64_t base = 0;
         int idx[RTR_MAXN];
-        for (int t = N - 2; t >= 1; --t) {
+        for (int t = N - 3; t >= 1; --t) {
             const int m = scyc[t];
             const uint32_t km = (uint32_t)sK[m];
             idx[t] = (int)(rem % km);
@@ -187,7 +195,13 @@ __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, do
             base += idx[t] * sstride[m];
         }
         __syncthreads();
-        {
+        // M = Z_{c_1}(i_1) ... Z_{c_{N-3}}(i_{N-3})  (Rb x R2; the identity when N = 3)
+        if (N == 3) {
+            for (int e = tid; e < Rb * Rb; e += blockDim.x) {
+                const int be = e / Rb, gg = e % Rb;
+                M0[be * RTR_MAX_RANK + gg] = (be == gg) ? T(1) : T(0);
+            }
+        } else {
             const int m = scyc[1];
             const int Rc = sR[(m + 1) % N];
             const int Km = sK[m];
@@ -198,7 +212,7 @@ __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, do
         }
         T* cur = M0;
         T* nxt = M1;
-        for (int t = 2; t <= N - 2; ++t) {
+        for (int t = 2; t <= N - 3; ++t) {
             __syncthreads();
             const int m = scyc[t];
             const int Rm = sR[m], Rc = sR[(m + 1) % N], Km = sK[m];
@@ -212,21 +226,35 @@ __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, do
             T* tmp = cur; cur = nxt; nxt = tmp;
         }
         __syncthreads();
-        for (int l0 = 0; l0 < Kl; l0 += LB) {
-            const int lb = min(LB, Kl - l0);
+        // M2[i2][be][g] = sum_c M[be][c] Z_{c_{N-2}}[c, i2, g]
+        for (int e = tid; e < K2 * Rb * Rl; e += blockDim.x) {
+            const int g = e % Rl, be = (e / Rl) % Rb, i2 = e / (Rl * Rb);
+            const T* z2 = Zc[m2] + i2 * Rl + g;
+            T sum = T(0);
+            for (int c = 0; c < R2; ++c) sum = dfma(cur[be * RTR_MAX_RANK + c], z2[c * K2 * Rl], sum);
+            M2[(i2 * Rb + be) * RTR_MAX_RANK + g] = sum;
+        }
+        __syncthreads();
+        for (int q0 = 0; q0 < nrows; q0 += LB) {
+            const int lb = min(LB, nrows - q0);
             if (s_on) {
-                const T* mrow = cur + s_be * RTR_MAX_RANK;
-                const T* zl = Zc[ml] + l0 * Rn + s_al;
                 for (int l = l_s; l < lb; l += s_pass) {
                     T sum = T(0);
-                    if (sc < C)
-                        for (int gg = 0; gg < Rl; ++gg) sum = dfma(mrow[gg], zl[gg * zst + l * Rn], sum);
+                    if (sc < C) {
+                        const int q = q0 + l, i2 = q / Kl, ll = q - i2 * Kl;
+                        const T* mrow = M2 + (i2 * Rb + s_be) * RTR_MAX_RANK;
+                        const T* zl = Zc[ml] + ll * Rn + s_al;
+                        for (int gg = 0; gg < Rl; ++gg) sum = dfma(mrow[gg], zl[gg * zst], sum);
+                    }
                     S[l * Cp + sc] = sum;
                 }
             }
             if (p_on) {
                 const T* prow = Pt + base + (int64_t)pi * str_n;
-                for (int l = l_p; l < lb; l += p_pass) Pv[l * Kn + pi] = prow[(int64_t)(l0 + l) * str_l];
+                for (int l = l_p; l < lb; l += p_pass) {
+                    const int q = q0 + l, i2 = q / Kl, ll = q - i2 * Kl;
+                    Pv[l * Kn + pi] = prow[(int64_t)i2 * str_2 + (int64_t)ll * str_l];
+                }
             }
             __syncthreads();
             if (wt.active) {
@@ -273,13 +301,15 @@ __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, do
 template <typename T>
 __global__ void __launch_bounds__(CT_THREADS) bcontract_kernel(const BTensor<T>* __restrict__ tens,
                                                                const CItem* __restrict__ items, int nitems, int N,
-                                                               int n, double* __restrict__ partial, int stage) {
+                                                               int n, double* __restrict__ partial, int stage,
+                                                               int k2max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* M0 = reinterpret_cast<T*>(smem_raw);          // 16 x 16
     T* M1 = M0 + RTR_MAX_RANK * RTR_MAX_RANK;        // 16 x 16
     T* S = M1 + RTR_MAX_RANK * RTR_MAX_RANK;         // LB x Cp (Cp <= 144)
     T* Pv = S + LB * 144;                            // LB x K_n (K_n <= 64)
-    T* Zs0 = Pv + LB * 64;                           // the other cores (if `stage`)
+    T* M2 = Pv + LB * 64;                            // k2max x 16 x 16
+    T* Zs0 = M2 + (size_t)k2max * RTR_MAX_RANK * RTR_MAX_RANK;   // the other cores (if `stage`)
     // this item's tensor descriptor, cached in shared memory: reading it from
     // the global BTensor inside the loops would repeat dependent global loads
     __shared__ int sK[RTR_MAXN], sR[RTR_MAXN], scyc[RTR_MAXN];
@@ -320,10 +350,10 @@ __global__ void __launch_bounds__(CT_THREADS) bcontract_kernel(const BTensor<T>*
         const int C = sR[(n + 1) % N] * sR[n];
         const rtr::WTile wt = rtr::wtile(C, sK[n]);
         switch (wt.ip) {
-#define RTR_IP_CASE(v) case v: bcontract_item<T, v>(ci, N, n, partial, sK, sR, scyc, sstride, Zc, sP, M0, M1, S, Pv, wt); break;
+#define RTR_IP_CASE(v) case v: bcontract_item<T, v>(ci, N, n, partial, sK, sR, scyc, sstride, Zc, sP, M0, M1, M2, S, Pv, wt); break;
             RTR_IP_CASE(1) RTR_IP_CASE(2) RTR_IP_CASE(3) RTR_IP_CASE(4) RTR_IP_CASE(5)
             RTR_IP_CASE(6) RTR_IP_CASE(7) RTR_IP_CASE(8) RTR_IP_CASE(9)
-            default: bcontract_item<T, rtr::TILE_IP>(ci, N, n, partial, sK, sR, scyc, sstride, Zc, sP, M0, M1, S, Pv, wt); break;
+            default: bcontract_item<T, rtr::TILE_IP>(ci, N, n, partial, sK, sR, scyc, sstride, Zc, sP, M0, M1, M2, S, Pv, wt); break;
 #undef RTR_IP_CASE
         }
     }
@@ -532,6 +562,7 @@ struct Impl {
     const double* tab = nullptr;
     size_t ct_smem = 0, sv_smem = 0;
     int ct_stage = 0;
+    int k2max = 1;                  // largest K of a mode streamed as c_{N-2} by the contraction
 };
 
 }  // namespace
@@ -628,11 +659,15 @@ int create_impl(Impl<T>** out, int count, int N, const int64_t* K, const int* R,
         double wsum = 0.0;
         for (int t = 0; t < count; ++t) {
             const BTensor<T>& b = h[t];
+            // a prefix fixes the cyclic modes n+1 .. n+N-3; the rows of one prefix
+            // run over the last two (n+N-2, n+N-1)
             int64_t J = 1;
-            for (int s = 1; s <= N - 2; ++s) J *= b.K[(n + s) % N];
-            const int ml = (n + N - 1) % N;
+            for (int s = 1; s <= N - 3; ++s) J *= b.K[(n + s) % N];
+            const int ml = (n + N - 1) % N, m2 = (n + N - 2) % N;
             const double C = (double)b.R[n] * b.R[(n + 1) % N];
-            const double per = (double)b.K[ml] * (C * b.R[ml] + (double)b.K[n] * C) + 4096.0;
+            const double rows = (double)b.K[m2] * b.K[ml];
+            const double per = rows * (C * b.R[ml] + (double)b.K[n] * C) +
+                               (double)b.K[m2] * b.R[(n + 1) % N] * b.R[ml] * b.R[m2] + 4096.0;
             jpre[t] = J;
             wpre[t] = per;
             wsum += per * J;
@@ -699,7 +734,11 @@ int create_impl(Impl<T>** out, int count, int N, const int64_t* K, const int* R,
             zmax = std::max(zmax, z);
         }
     (void)maxKn;
-    m->ct_smem = sizeof(T) * (2 * RTR_MAX_RANK * RTR_MAX_RANK + LB * 144 + LB * 64);
+    m->k2max = 1;
+    for (int t = 0; t < count; ++t)
+        for (int n = 0; n < N; ++n) m->k2max = std::max<int>(m->k2max, (int)h[t].K[(n + N - 2) % N]);
+    m->ct_smem = sizeof(T) * (2 * RTR_MAX_RANK * RTR_MAX_RANK + LB * 144 + LB * 64 +
+                              (size_t)m->k2max * RTR_MAX_RANK * RTR_MAX_RANK);
     m->ct_stage = (m->ct_smem + sizeof(T) * zmax <= 96 * 1024) ? 1 : 0;
     if (m->ct_stage) m->ct_smem += sizeof(T) * zmax;
     m->sv_smem = sizeof(T) * (size_t)cmax * cmax;
@@ -730,7 +769,7 @@ int run_impl(Impl<T>* m, double* err, cudaStream_t s) {
                 m->d_tens, m->d_gitems[n], m->n_gitems[n], N, (n + 1) % N, N - 1, 0);
             RTR_LAUNCH_CHECK("bgram_kernel");
             contract<<<(unsigned)std::min(m->n_citems[n], 4 * m->num_sms), CT_THREADS, m->ct_smem, s>>>(
-                m->d_tens, m->d_citems[n], m->n_citems[n], N, n, m->partial, m->ct_stage);
+                m->d_tens, m->d_citems[n], m->n_citems[n], N, n, m->partial, m->ct_stage, m->k2max);
             RTR_LAUNCH_CHECK("bcontract_kernel");
             solve<<<m->count, SV_THREADS, m->sv_smem, s>>>(m->d_tens, N, n, m->partial, sw, m->sweeps, err,
                                                            m->flags, (int)(m->sv_smem / sizeof(T)));

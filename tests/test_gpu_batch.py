@@ -120,3 +120,33 @@ def test_batch_argument_errors():
     params.chain_order[0] = 2
     with pytest.raises(rtr.RtrError):
         rtr.rtr_batch_create([(8, 8, 8)], [(4, 4, 4)], [(2, 2, 2)], params)
+
+
+def _order_batch(order, count, lo, hi, rlo, rhi, seed):
+    """Order-3 or order-5 TR tensors of the batched recipe (the contraction
+    streams the last two cyclic modes of every update: an empty prefix for
+    order 3, a one-product prefix chain for order 5)."""
+    rng = np.random.default_rng(seed)
+    shapes, Xs, Ks, Rs = [], [], [], []
+    for t in range(count):
+        dims = tuple(int(x) for x in rng.integers(lo, hi + 1, size=order))
+        r = int(rng.integers(rlo, rhi + 1))
+        S = ot.tr_full(workloads.smoothed_tr_cores(dims, r, seed + 31 * t))
+        shapes.append(dims)
+        Xs.append(workloads.to_pixels(S))
+        K, R = workloads.batch_ranks(dims, r)
+        Ks.append(K)
+        Rs.append(R)
+    return shapes, Xs, Ks, Rs
+
+
+@pytest.mark.parametrize("order,prec", [(3, "fp64"), (5, "fp64"), (3, "bf16"), (5, "bf16")])
+def test_batch_orders_3_and_5_vs_oracle(order, prec):
+    lo, hi = (8, 20) if order == 3 else (5, 9)
+    shapes, Xs, Ks, Rs = _order_batch(order, 5, lo, hi, 2, 3, 120 + order)
+    _, outs = run_batch(shapes, Xs, Ks, Rs, prec, 121, 4, nstreams=2)
+    cores, rse = outs[0]
+    refs = oracle_batch(Xs, Ks, Rs, prec, 121, 4)
+    tol = 1e-10 if prec == "fp64" else 1e-3
+    for t in range(len(shapes)):
+        assert rel(ot.tr_full(cores[t]), refs[t][0]) <= tol, (t, shapes[t], Rs[t])
