@@ -238,22 +238,27 @@ __device__ __forceinline__ void bcontract_item(const CItem& ci, int N, int n, do
         for (int q0 = 0; q0 < nrows; q0 += LB) {
             const int lb = min(LB, nrows - q0);
             if (s_on) {
+                // row q = q0 + l -> (i2, ll) = divmod(q, Kl), advanced by s_pass
+                int i2 = (q0 + l_s) / Kl, ll = (q0 + l_s) - i2 * Kl;
                 for (int l = l_s; l < lb; l += s_pass) {
                     T sum = T(0);
                     if (sc < C) {
-                        const int q = q0 + l, i2 = q / Kl, ll = q - i2 * Kl;
                         const T* mrow = M2 + (i2 * Rb + s_be) * RTR_MAX_RANK;
                         const T* zl = Zc[ml] + ll * Rn + s_al;
                         for (int gg = 0; gg < Rl; ++gg) sum = dfma(mrow[gg], zl[gg * zst], sum);
                     }
                     S[l * Cp + sc] = sum;
+                    ll += s_pass;
+                    while (ll >= Kl) { ll -= Kl; ++i2; }
                 }
             }
             if (p_on) {
                 const T* prow = Pt + base + (int64_t)pi * str_n;
+                int i2 = (q0 + l_p) / Kl, ll = (q0 + l_p) - i2 * Kl;
                 for (int l = l_p; l < lb; l += p_pass) {
-                    const int q = q0 + l, i2 = q / Kl, ll = q - i2 * Kl;
                     Pv[l * Kn + pi] = prow[(int64_t)i2 * str_2 + (int64_t)ll * str_l];
+                    ll += p_pass;
+                    while (ll >= Kl) { ll -= Kl; ++i2; }
                 }
             }
             __syncthreads();
