@@ -143,13 +143,18 @@ int rtr_project(rtr_plan* plan, const void* X, const double* const* Y,
  * Algorithm 1, step 9 with TR-ALS: fit cores Z_n (R_n x K_n x R_{n+1},
  * float64) to P by `sweeps` sweeps of exact least-squares core updates
  * (Eq. 2: P_<n> = Z_{n,(2)} S^T, S the subchain; Z_{n,(2)} = P_<n> S (S^T S)^-1,
- * the Gram S^T S formed from float64 transfer matrices and solved in float64).
+ * the Gram S^T S formed from float64 transfer matrices and solved to float64
+ * accuracy: a float32 inverse refined with double-float residuals).
  * Z: in/out.  If init_given != 0 the Z buffers hold the starting cores;
  * otherwise the library writes its default start (discrete-Gaussian cores
  * from Philox4x64-10 with key (seed + 1, 256 + n), scaled so ||TR(Z)|| = ||P||).
  * err: device float64[sweeps] (may be NULL) receives ||P - TR(Z)||_F after
  * each sweep.  Requires R_n R_{n+1} <= 144 for every n (else
- * RTR_EUNSUPPORTED).
+ * RTR_EUNSUPPORTED).  The first call with a given (P, Z, err, init_given)
+ * records the sweeps into a CUDA graph on a stream of the plan and later calls
+ * with the same pointers replay it on `stream` (a call while `stream` is being
+ * captured runs eagerly and is recorded by the caller's capture); calling with
+ * new pointers synchronises the device once and records again.
  */
 int rtr_als(rtr_plan* plan, const void* P, double* const* Z, int init_given,
             double* err, void* stream);

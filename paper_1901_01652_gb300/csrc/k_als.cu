@@ -28,37 +28,54 @@ namespace {
 // With Zfirst set (and Sprev null), the previous level is the first core
 // itself, read in its own layout Zfirst[beta, j', c] (Jp = its mode length).
 // IDX: index type of the element decode (uint32_t when every index fits:
-// a 64-bit division is a long instruction sequence per element)
-template <typename T, typename TZ, typename IDX>
+// a 64-bit division is a long instruction sequence per element).  TG: outputs
+// per thread along gamma (consecutive), which share the loads of Sprev's row.
+template <typename T, typename TZ, typename IDX, int TG>
 __global__ void subchain_step_kernel(const T* __restrict__ Sprev, int64_t Jp_, int Rb, int Rc,
                                      const TZ* __restrict__ Z, int Km, int Rd, T* __restrict__ Sout,
                                      int final_tr, int64_t Aa_, int64_t Bb_, const TZ* __restrict__ Zfirst) {
     const IDX Jp = (IDX)Jp_, Aa = (IDX)Aa_, Bb = (IDX)Bb_;
-    const IDX total = Jp * (IDX)Km * (IDX)Rb * (IDX)Rd;
+    const int Rq = (Rd + TG - 1) / TG;
+    const IDX total = Jp * (IDX)Km * (IDX)Rb * (IDX)Rq;
     for (IDX e = blockIdx.x * (IDX)blockDim.x + threadIdx.x; e < total; e += (IDX)gridDim.x * blockDim.x) {
-        const int g = (int)(e % (IDX)Rd);
-        const IDX q = e / (IDX)Rd;
+        const int g0 = (int)(e % (IDX)Rq) * TG;
+        const IDX q = e / (IDX)Rq;
         const int be = (int)(q % (IDX)Rb);
         const IDX j = q / (IDX)Rb;
         const int i = (int)(j % (IDX)Km);
         const IDX jp = j / (IDX)Km;
-        T v;
+        T v[TG];
+#pragma unroll
+        for (int t = 0; t < TG; ++t) v[t] = T(0);
+        const TZ* zc = Z + (IDX)i * (IDX)Rd + (IDX)g0;      // Z[c, i, g0 + t] = zc[c Km Rd + t]
+        const IDX zs = (IDX)Km * (IDX)Rd;
         if (Zfirst != nullptr) {
-            T acc = T(0);
             const TZ* zf = Zfirst + ((IDX)be * Jp + jp) * (IDX)Rc;
-            for (int c = 0; c < Rc; ++c) acc = fma((T)zf[c], (T)Z[((IDX)c * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)g], acc);
-            v = acc;
+            for (int c = 0; c < Rc; ++c) {
+                const T f = (T)zf[c];
+#pragma unroll
+                for (int t = 0; t < TG; ++t)
+                    if (g0 + t < Rd) v[t] = fma(f, (T)zc[(IDX)c * zs + t], v[t]);
+            }
         } else if (Sprev == nullptr) {
-            v = (T)Z[((IDX)be * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)g];
+#pragma unroll
+            for (int t = 0; t < TG; ++t)
+                if (g0 + t < Rd) v[t] = (T)Z[((IDX)be * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)(g0 + t)];
         } else {
-            T sum = T(0);
             const T* sp = Sprev + (jp * (IDX)Rb + (IDX)be) * (IDX)Rc;
-            for (int c = 0; c < Rc; ++c) sum = fma(sp[c], (T)Z[((IDX)c * (IDX)Km + (IDX)i) * (IDX)Rd + (IDX)g], sum);
-            v = sum;
+            for (int c = 0; c < Rc; ++c) {
+                const T f = sp[c];
+#pragma unroll
+                for (int t = 0; t < TG; ++t)
+                    if (g0 + t < Rd) v[t] = fma(f, (T)zc[(IDX)c * zs + t], v[t]);
+            }
         }
         IDX r = j;
         if (final_tr) { const IDX b = j / Aa, a = j % Aa; r = a * Bb + b; }
-        Sout[(r * (IDX)Rb + (IDX)be) * (IDX)Rd + (IDX)g] = v;
+        T* out = Sout + (r * (IDX)Rb + (IDX)be) * (IDX)Rd + (IDX)g0;
+#pragma unroll
+        for (int t = 0; t < TG; ++t)
+            if (g0 + t < Rd) out[t] = v[t];
     }
 }
 
@@ -204,6 +221,9 @@ __global__ void __launch_bounds__(256) gram_inverse_kernel(const float* __restri
     __shared__ float v[2][16 * T];
     __shared__ float sc[16 * T];
     const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+    // this kernel is the flag's only writer in an update, and runs after the
+    // previous update's solve (stream order): clear it for this update
+    if (tid == 0) *need_slow = 0;
     int ok = 1;
     for (int c = tid; c < 16 * T; c += blockDim.x) {
         float s = 0.f;
@@ -294,6 +314,79 @@ __global__ void __launch_bounds__(256) gram_inverse_kernel(const float* __restri
     }
 }
 
+// Slow path of a core update (one CTA, run by the solve kernel's first CTA
+// when the Gram inverse raised *need_slow): float64
+// Cholesky of G in shared memory and direct solves, or, if G is not SPD in
+// float64 either, the eigen-pseudo-inverse with cutoff 1e-13 lambda_max
+// (Jacobi eigendecomposition in global scratch).
+__device__ void solve_slow_body(const double* __restrict__ Mprod, int Rn, int Rn1,
+                                                             int In, const double* __restrict__ W,
+                                                             double* __restrict__ Wz, double* __restrict__ Zn,
+                                                             float* __restrict__ Znf, double* __restrict__ zw_out,
+                                                             double* __restrict__ jac_ws, int* __restrict__ need_slow,
+                                                             int* __restrict__ flags) {
+    extern __shared__ __align__(16) double Gs[];
+    const int C = Rn * Rn1;
+    const int ld = C + 1;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Gs[(e / C) * ld + e % C] = Mprod[e];
+    for (int e = threadIdx.x; e < In * C; e += blockDim.x) Wz[e] = W[e];
+    __syncthreads();
+    int ok = 1;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x)
+        if (!isfinite(Gs[(e / C) * ld + e % C])) ok = 0;
+    ok = __syncthreads_and(ok);
+    if (ok) ok = rtr::block_cholesky(Gs, C, ld) ? 1 : 0;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (ok) {
+        for (int i = warp; i < In; i += nw) rtr::warp_chol_solve(Gs, C, ld, Wz + (int64_t)i * C);
+        __syncthreads();
+    } else {
+        // pseudo-inverse with cutoff 1e-13 * lambda_max (Jacobi eigendecomposition)
+        if (threadIdx.x == 0) atomicOr(flags, RTR_FLAG_GRAM_PINV);
+        double* Aj = jac_ws;
+        double* V = jac_ws + (int64_t)C * C;
+        __shared__ int pairs[2 * 160];
+        __shared__ double cs[2 * 160];
+        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Aj[e] = Mprod[e];
+        __syncthreads();
+        rtr::block_jacobi_eig<double>(Aj, V, C, C, pairs, cs, 40, 1e-30);
+        double lmax = 0.0;
+        for (int c = 0; c < C; ++c) lmax = fmax(lmax, Aj[c * C + c]);
+        const double cut = 1e-13 * lmax;
+        // z = w V diag(1/lambda) V^T  (row vectors), using Wz as scratch per row
+        for (int i = 0; i < In; ++i) {
+            __shared__ double t[160];
+            for (int c = threadIdx.x; c < C; c += blockDim.x) {
+                double s = 0.0;
+                for (int l = 0; l < C; ++l) s += W[(int64_t)i * C + l] * V[l * C + c];
+                const double lam = Aj[c * C + c];
+                t[c] = (lam > cut) ? s / lam : 0.0;
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < C; c += blockDim.x) {
+                double s = 0.0;
+                for (int l = 0; l < C; ++l) s += t[l] * V[c * C + l];
+                Wz[(int64_t)i * C + c] = s;
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < In * C; e += blockDim.x) {
+        const int i = e / C, c = e % C;
+        const int be = c / Rn, al = c % Rn;
+        Zn[((int64_t)al * In + i) * Rn1 + be] = Wz[e];
+        if (Znf) Znf[((int64_t)al * In + i) * Rn1 + be] = (float)Wz[e];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < In; i += blockDim.x) {
+        double zw = 0.0;
+        for (int c = 0; c < C; ++c) zw += Wz[(int64_t)i * C + c] * W[(int64_t)i * C + c];
+        zw_out[i] = zw;
+    }
+    __syncthreads();
+    (void)need_slow;
+}
+
 // Core update for slice i of mode n (one CTA per slice): z_i solves
 // G z_i = w_i by iterative refinement (Wilkinson; Moler 1967) with the
 // float32 inverse from gram_inverse_kernel:
@@ -319,12 +412,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __global__ void __launch_bounds__(SOLVE_THREADS) als_solve_inv_kernel(
     const float* __restrict__ Gh, const float* __restrict__ Gl, const float* __restrict__ Ginv, int Rn, int Rn1,
     int In, const double* __restrict__ W, double* __restrict__ Zn, float* __restrict__ Znf,
-    double* __restrict__ zw_out, const int* __restrict__ need_slow, float tol2, int max_it) {
-    extern __shared__ __align__(16) float gi[];          // C x C
+    double* __restrict__ zw_out, int* __restrict__ need_slow, float tol2, int max_it,
+    const double* __restrict__ G, double* __restrict__ Wz, double* __restrict__ jac, int* __restrict__ flags) {
+    extern __shared__ __align__(16) float gi[];          // C x C (the slow path: C x (C + 1) float64)
     __shared__ float wh[SOLVE_MAXC], wl[SOLVE_MAXC], zh[SOLVE_MAXC], zl[SOLVE_MAXC], rf[SOLVE_MAXC];
     __shared__ float redf[2][32];
     __shared__ double red[32];
-    if (*(volatile const int*)need_slow) return;
+    if (*(volatile const int*)need_slow) {
+        // the inverse met a non-positive pivot: the first CTA solves every slice in float64
+        if (blockIdx.x == 0) solve_slow_body(G, Rn, Rn1, In, W, Wz, Zn, Znf, zw_out, jac, need_slow, flags);
+        return;
+    }
     const int C = Rn * Rn1;
     const int i = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -431,78 +529,6 @@ __global__ void als_err_kernel(const double* __restrict__ zw, int In, const doub
     }
 }
 
-// Slow path (runs only if the Gram inverse raised *need_slow): float64
-// Cholesky of G in shared memory and direct solves, or, if G is not SPD in
-// float64 either, the eigen-pseudo-inverse with cutoff 1e-13 lambda_max
-// (Jacobi eigendecomposition in global scratch).
-__global__ void __launch_bounds__(512) als_solve_slow_kernel(const double* __restrict__ Mprod, int Rn, int Rn1,
-                                                             int In, const double* __restrict__ W,
-                                                             double* __restrict__ Wz, double* __restrict__ Zn,
-                                                             float* __restrict__ Znf, double* __restrict__ zw_out,
-                                                             double* __restrict__ jac_ws, int* __restrict__ need_slow,
-                                                             int* __restrict__ flags) {
-    if (*(volatile int*)need_slow == 0) return;
-    extern __shared__ __align__(16) double Gs[];
-    const int C = Rn * Rn1;
-    const int ld = C + 1;
-    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Gs[(e / C) * ld + e % C] = Mprod[e];
-    for (int e = threadIdx.x; e < In * C; e += blockDim.x) Wz[e] = W[e];
-    __syncthreads();
-    int ok = 1;
-    for (int e = threadIdx.x; e < C * C; e += blockDim.x)
-        if (!isfinite(Gs[(e / C) * ld + e % C])) ok = 0;
-    ok = __syncthreads_and(ok);
-    if (ok) ok = rtr::block_cholesky(Gs, C, ld) ? 1 : 0;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (ok) {
-        for (int i = warp; i < In; i += nw) rtr::warp_chol_solve(Gs, C, ld, Wz + (int64_t)i * C);
-        __syncthreads();
-    } else {
-        // pseudo-inverse with cutoff 1e-13 * lambda_max (Jacobi eigendecomposition)
-        if (threadIdx.x == 0) atomicOr(flags, RTR_FLAG_GRAM_PINV);
-        double* Aj = jac_ws;
-        double* V = jac_ws + (int64_t)C * C;
-        __shared__ int pairs[2 * 160];
-        __shared__ double cs[2 * 160];
-        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Aj[e] = Mprod[e];
-        __syncthreads();
-        rtr::block_jacobi_eig<double>(Aj, V, C, C, pairs, cs, 40, 1e-30);
-        double lmax = 0.0;
-        for (int c = 0; c < C; ++c) lmax = fmax(lmax, Aj[c * C + c]);
-        const double cut = 1e-13 * lmax;
-        // z = w V diag(1/lambda) V^T  (row vectors), using Wz as scratch per row
-        for (int i = 0; i < In; ++i) {
-            __shared__ double t[160];
-            for (int c = threadIdx.x; c < C; c += blockDim.x) {
-                double s = 0.0;
-                for (int l = 0; l < C; ++l) s += W[(int64_t)i * C + l] * V[l * C + c];
-                const double lam = Aj[c * C + c];
-                t[c] = (lam > cut) ? s / lam : 0.0;
-            }
-            __syncthreads();
-            for (int c = threadIdx.x; c < C; c += blockDim.x) {
-                double s = 0.0;
-                for (int l = 0; l < C; ++l) s += t[l] * V[c * C + l];
-                Wz[(int64_t)i * C + c] = s;
-            }
-            __syncthreads();
-        }
-    }
-    for (int e = threadIdx.x; e < In * C; e += blockDim.x) {
-        const int i = e / C, c = e % C;
-        const int be = c / Rn, al = c % Rn;
-        Zn[((int64_t)al * In + i) * Rn1 + be] = Wz[e];
-        if (Znf) Znf[((int64_t)al * In + i) * Rn1 + be] = (float)Wz[e];
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < In; i += blockDim.x) {
-        double zw = 0.0;
-        for (int c = 0; c < C; ++c) zw += Wz[(int64_t)i * C + c] * W[(int64_t)i * C + c];
-        zw_out[i] = zw;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *need_slow = 0;
-}
 
 // Default start: entry e of core n is the fp64 table value at field e % 20 of
 // Philox4x64-10(counter (e/20, 0, 0, 0), key (seed + 1, 256 + n)).
@@ -668,14 +694,16 @@ T* build_chain(int N, const int64_t* dims, const int* R, const TZ* const* Z, int
         T* out = bufs[which];
         const int fin = (t == count - 1) ? final_tr : 0;
         const int64_t total = Jp * Km * Rfirst * Rd;
-        // 32-bit decode when the output (and so every index) stays below 2^31
+        // 32-bit decode when the output (and so every index) stays below 2^31;
+        // four consecutive gamma per thread (shared loads of the previous level)
         const int64_t outsz = std::max<int64_t>(total, Aa * Bb * Rfirst * Rd);
+        const int64_t nthr = Jp * Km * Rfirst * ((Rd + 3) / 4);
         if (outsz < ((int64_t)1 << 31))
-            subchain_step_kernel<T, TZ, uint32_t><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out,
-                                                                              fin, Aa, Bb, t == t0 ? zfirst : nullptr);
+            subchain_step_kernel<T, TZ, uint32_t, 4><<<grid_for(nthr), 256, 0, s>>>(
+                cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out, fin, Aa, Bb, t == t0 ? zfirst : nullptr);
         else
-            subchain_step_kernel<T, TZ, int64_t><<<grid_for(total), 256, 0, s>>>(cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out,
-                                                                             fin, Aa, Bb, t == t0 ? zfirst : nullptr);
+            subchain_step_kernel<T, TZ, int64_t, 4><<<grid_for(nthr), 256, 0, s>>>(
+                cur, Jp, Rfirst, Rc, Z[m], Km, Rd, out, fin, Aa, Bb, t == t0 ? zfirst : nullptr);
         rtr_count_launch();
         if (cudaGetLastError() != cudaSuccess) { *status = RTR_ECUDA; return nullptr; }
         cur = out;
@@ -795,8 +823,6 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
         int cmax = 0;
         for (int n = 0; n < N; ++n) cmax = std::max(cmax, p->R[n] * p->R[(n + 1) % N]);
         RTR_CUDA(cudaFuncSetAttribute(als_solve_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(float) * (size_t)cmax * cmax)));
-        RTR_CUDA(cudaFuncSetAttribute(als_solve_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * (size_t)cmax * (cmax + 1))));
     }
     for (int sweep = 0; sweep < p->params.sweeps; ++sweep) {
@@ -848,14 +874,12 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             // (relative error ~(kappa 2^-24)^2)
             const float tol2 = is_f64 ? 1e-28f : 1e-18f;
             const int max_it = is_f64 ? 12 : 2;
-            const size_t gsmem = sizeof(float) * (size_t)C * C;
+            // dynamic shared memory: the float32 inverse, or the slow path's float64 Gram matrix
+            const size_t gsmem = std::max(sizeof(float) * (size_t)C * C, sizeof(double) * (size_t)C * (C + 1));
             als_solve_inv_kernel<<<(unsigned)I, SOLVE_THREADS, gsmem, s>>>(Gf, Gfl, Ginv, Rn, Rn1, (int)I, W, Z[n],
-                                                                          Zf[n], zw, need_slow, tol2, max_it);
+                                                                          Zf[n], zw, need_slow, tol2, max_it, G, Wz,
+                                                                          jac, p->flags);
             RTR_LAUNCH_CHECK("als_solve_inv_kernel");
-            const size_t ssmem = sizeof(double) * (size_t)C * (C + 1);
-            als_solve_slow_kernel<<<1, 512, ssmem, s>>>(G, Rn, Rn1, (int)I, W, Wz, Z[n], Zf[n], zw, jac,
-                                                        need_slow, p->flags);
-            RTR_LAUNCH_CHECK("als_solve_slow_kernel");
             if (err && n == N - 1) {
                 als_err_kernel<<<1, 32, 0, s>>>(zw, (int)I, normP2, err + sweep);
                 RTR_LAUNCH_CHECK("als_err_kernel");
@@ -914,13 +938,61 @@ int run_reconstruct(int N, const int64_t* dims, const int* R, const double* cons
     return reconstruct_impl<float>(N, dims, R, G, (float*)Xhat, work, work_bytes, s);
 }
 
+static int als_eager(rtr_plan* p, const void* P, double* const* Z, int init_given, double* err, cudaStream_t s) {
+    if (p->params.prec == RTR_FP64) return als_impl<double>(p, (const double*)P, Z, init_given, err, s);
+    return als_impl<float>(p, (const float*)P, Z, init_given, err, s);
+}
+
+// The sweeps are a long chain of small dependent kernels on two streams; they
+// are recorded once into a CUDA graph per argument set (P, Z, err,
+// init_given) on the plan's own stream and replayed on the caller's stream,
+// which removes the per-launch gaps.  A call made while the caller's stream is
+// being captured runs eagerly (the caller's capture records it); if recording
+// fails the call runs eagerly too.
 int run_als(rtr_plan* p, const void* P, double* const* Z, int init_given, double* err, cudaStream_t s) {
     for (int n = 0; n < p->N; ++n) {
         if (p->R[n] * p->R[(n + 1) % p->N] > 144)
             return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS supports R_n R_{n+1} <= 144");
     }
-    if (p->params.prec == RTR_FP64) return als_impl<double>(p, (const double*)P, Z, init_given, err, s);
-    return als_impl<float>(p, (const float*)P, Z, init_given, err, s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RTR_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return als_eager(p, P, Z, init_given, err, s);
+    bool same = p->als_exec != nullptr && p->als_key_P == P && p->als_key_err == err &&
+                p->als_key_init == (init_given != 0);
+    for (int n = 0; same && n < p->N; ++n) same = p->als_key_Z[n] == Z[n];
+    if (!same) {
+        if (p->als_exec) {
+            // new arguments (rare): let any replay of the old graph finish first
+            RTR_CUDA(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(p->als_exec);
+            p->als_exec = nullptr;
+        }
+        const unsigned long long before = rtr_kernel_launches();
+        RTR_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        const int st = als_eager(p, P, Z, init_given, err, p->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(p->cap, &g);
+        const long long recorded = (long long)(rtr_kernel_launches() - before);
+        rtr_count_launches(-recorded);              // recorded, not run
+        cudaGraphExec_t ex = nullptr;
+        if (st == RTR_OK && ee == cudaSuccess && g != nullptr &&
+            cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+            p->als_exec = ex;
+            p->als_kernels = recorded;
+            p->als_key_P = P;
+            p->als_key_err = err;
+            p->als_key_init = (init_given != 0);
+            for (int n = 0; n < p->N; ++n) p->als_key_Z[n] = Z[n];
+        }
+        if (g) cudaGraphDestroy(g);
+        if (!p->als_exec) {
+            cudaGetLastError();
+            return als_eager(p, P, Z, init_given, err, s);
+        }
+    }
+    RTR_CUDA(cudaGraphLaunch(p->als_exec, s));
+    rtr_count_launches(p->als_kernels);
+    return RTR_OK;
 }
 
 int run_backproject(rtr_plan* p, const double* const* Z, const double* const* Q, double* const* G, const int* ranks,

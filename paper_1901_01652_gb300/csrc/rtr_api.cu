@@ -118,6 +118,8 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
     cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws);
     for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
+    if (p->als_exec) cudaGraphExecDestroy(p->als_exec);
+    if (p->cap) cudaStreamDestroy(p->cap);
     if (p->side) cudaStreamDestroy(p->side);
     delete p;
 }
@@ -144,6 +146,7 @@ void rtr_host_tables(double* t64, float* t32) {
 
 static std::atomic<unsigned long long> g_launches{0};
 void rtr_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void rtr_count_launches(long long delta) { g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed); }
 
 int rtr_cuda_check(cudaError_t e, const char* what) {
     return rtr_set_error(RTR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -308,6 +311,7 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
         p->sub_ws[0] = sb; p->sub_ws[1] = sb + sub_bytes; p->sub_bytes = sub_bytes;
     }
     RTR_TRYC(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    RTR_TRYC(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     for (int e = 0; e < 4; ++e) RTR_TRYC(cudaEventCreateWithFlags(&p->ev[e], cudaEventDisableTiming));
     RTR_TRY(dalloc(&p->flags, 4));
     RTR_TRYC(cudaMemset(p->flags, 0, 4 * sizeof(int)));

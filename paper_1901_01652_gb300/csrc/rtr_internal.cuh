@@ -41,6 +41,15 @@ struct rtr_plan {
     size_t als_maxK = 0;         // max K_n
     cudaStream_t side = nullptr; // second stream for work that overlaps the caller's stream
     cudaEvent_t ev[4] = {};
+    // TR-ALS replay: the sweeps of rtr_als recorded once (on `cap`, a stream of
+    // the plan) per argument set and replayed on the caller's stream
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t als_exec = nullptr;
+    const void* als_key_P = nullptr;
+    double* als_key_Z[RTR_MAXN] = {};
+    double* als_key_err = nullptr;
+    int als_key_init = -1;
+    long long als_kernels = 0;   // kernels in the recorded graph (counted at each replay)
     void* sub_ws[2] = {nullptr, nullptr}; size_t sub_bytes = 0;  // subchain ping-pong
     int* flags = nullptr;
     void* tc_ws = nullptr;       size_t tc_ws_bytes = 0;       // tensor-core path workspace
@@ -54,6 +63,7 @@ int rtr_cuda_check(cudaError_t e, const char* what);
 // every kernel launch of the library is followed by this check, which also
 // counts the launch (rtr_kernel_launches)
 void rtr_count_launch();
+void rtr_count_launches(long long delta);
 #define RTR_LAUNCH_CHECK(what) do { rtr_count_launch(); cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return rtr_cuda_check(e_, what); } while (0)
 
 static inline int64_t rtr_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
