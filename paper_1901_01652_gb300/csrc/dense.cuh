@@ -88,8 +88,14 @@ __device__ inline double block_sum(double v, double* red /* >= 32 doubles */) {
 // disjoint rotations per step), in the arithmetic type T.  On return the
 // diagonal of A holds the eigenvalues and the columns of V (n x n, ld) the
 // eigenvectors.  `pairs` needs 2*((n+1)/2) ints, `cs` needs 2*((n+1)/2) T.
-// A sweep ends the iteration once the off-diagonal mass is at most
-// off_tol times the total (block-wide reduction, every thread takes part).
+// A pair is rotated only while |a_pq| > eps_T sqrt(|a_pp a_qq|) (eps_T the
+// unit roundoff of T; the relative rule of Demmel and Veselic, 1992) and
+// |a_pq| > eps_T ||A||_F: entries below the second bound are rounding noise
+// of the rotations themselves, which would otherwise keep a numerically
+// singular block rotating forever in float32.  The iteration stops after the
+// first sweep that rotates nothing, once the off-diagonal mass is at most
+// off_tol times the total (block-wide reduction, every thread takes part),
+// or after max_sweeps.
 template <typename T>
 __device__ inline void block_jacobi_eig(T* A, T* V, int n, int ld, int* pairs, T* cs, int max_sweeps,
                                         T off_tol) {
@@ -101,6 +107,7 @@ __device__ inline void block_jacobi_eig(T* A, T* V, int n, int ld, int* pairs, T
     const int np = m / 2;
     __shared__ T red_off[32], red_tot[32];
     const int lane = tid & 31, w = tid >> 5, nw = (nt + 31) >> 5;
+    const T eps = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08);
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         // convergence test: off-diagonal mass relative to the whole
         T off = T(0), tot = T(0);
@@ -120,6 +127,8 @@ __device__ inline void block_jacobi_eig(T* A, T* V, int n, int ld, int* pairs, T
         for (int u = 0; u < nw; ++u) { off += red_off[u]; tot += red_tot[u]; }
         __syncthreads();
         if (!(off > off_tol * tot)) break;
+        const T floor_abs = eps * sqrt(tot);
+        int rotated = 0;
         for (int step = 0; step < m - 1; ++step) {
             // round-robin pairing: player 0 fixed, others rotate
             for (int k = tid; k < np; k += nt) {
@@ -130,8 +139,9 @@ __device__ inline void block_jacobi_eig(T* A, T* V, int n, int ld, int* pairs, T
                 T c = T(1), sn = T(0);
                 if (q < n) {
                     const T apq = A[p * ld + q];
-                    if (apq != T(0)) {
-                        const T app = A[p * ld + p], aqq = A[q * ld + q];
+                    const T app = A[p * ld + p], aqq = A[q * ld + q];
+                    if (fabs(apq) > eps * sqrt(fabs(app)) * sqrt(fabs(aqq)) && fabs(apq) > floor_abs) {
+                        rotated = 1;
                         const T tau = (aqq - app) / (T(2) * apq);
                         const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
                         c = T(1) / sqrt(T(1) + t * t);
@@ -167,7 +177,121 @@ __device__ inline void block_jacobi_eig(T* A, T* V, int n, int ld, int* pairs, T
             }
             __syncthreads();
         }
+        if (!__syncthreads_or(rotated)) break;
     }
+}
+
+// Shared-memory form of the same cyclic Jacobi iteration (same pairing,
+// thresholds and stopping rules as block_jacobi_eig).  A round applies the
+// n/2 disjoint rotations from both sides at once: with pairs (p, q) and
+// (r, u), block [p q] x [r u] of J^T A J is J_pq^T A[pq, ru] J_ru, so each
+// thread reads one 2 x 2 block of the current buffer and writes it to the
+// other (no read/write hazard: two barriers per round, one after the
+// rotation parameters, one after the update).  Diagonal blocks take the
+// classical update a_pp -= t a_pq, a_qq += t a_pq, a_pq = 0.
+// A0 holds the input (n x n, ld), A1 and V are n x ld scratch; cs needs
+// 3 * np T and pairs 2 * np ints (np = ceil(n / 2)).  Returns the buffer
+// (A0 or A1) whose diagonal holds the eigenvalues; V's columns are the
+// eigenvectors.
+template <typename T>
+__device__ inline T* block_jacobi_eig_db(T* A0, T* A1, T* V, int n, int ld, int* pairs, T* cs, int max_sweeps,
+                                         T off_tol) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? T(1) : T(0);
+    if (n < 2) { __syncthreads(); return A0; }
+    const int m = (n + 1) & ~1;
+    const int np = m / 2;
+    __shared__ T red_off[32], red_tot[32];
+    const int lane = tid & 31, w = tid >> 5, nw = (nt + 31) >> 5;
+    const T eps = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08);
+    T* cur = A0;
+    T* nxt = A1;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        T off = T(0), tot = T(0);
+        __syncthreads();
+        for (int e = tid; e < n * n; e += nt) {
+            const int i = e / n, j = e % n;
+            const T a = cur[i * ld + j];
+            tot += a * a;
+            if (i != j) off += a * a;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (lane == 0) { red_off[w] = off; red_tot[w] = tot; }
+        __syncthreads();
+        off = T(0); tot = T(0);
+        for (int u = 0; u < nw; ++u) { off += red_off[u]; tot += red_tot[u]; }
+        if (!(off > off_tol * tot)) break;
+        const T floor_abs = eps * sqrt(tot);
+        int rotated = 0;
+        for (int step = 0; step < m - 1; ++step) {
+            for (int k = tid; k < np; k += nt) {
+                int p = (k == 0) ? 0 : 1 + (k - 1 + step) % (m - 1);
+                int q = 1 + (m - 2 - k + step) % (m - 1);
+                if (p > q) { const int t = p; p = q; q = t; }
+                pairs[2 * k] = p; pairs[2 * k + 1] = q;
+                T c = T(1), sn = T(0), tt = T(0);
+                if (q < n) {
+                    const T apq = cur[p * ld + q];
+                    const T app = cur[p * ld + p], aqq = cur[q * ld + q];
+                    if (fabs(apq) > eps * sqrt(fabs(app)) * sqrt(fabs(aqq)) && fabs(apq) > floor_abs) {
+                        rotated = 1;
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                        c = T(1) / sqrt(T(1) + tt * tt);
+                        sn = tt * c;
+                    }
+                }
+                cs[3 * k] = c; cs[3 * k + 1] = sn; cs[3 * k + 2] = tt;
+            }
+            __syncthreads();
+            for (int e = tid; e < np * np; e += nt) {
+                const int k = e / np, l = e % np;
+                const int p = pairs[2 * k], q = pairs[2 * k + 1];
+                const int r = pairs[2 * l], u = pairs[2 * l + 1];
+                if (k == l) {
+                    if (q < n) {
+                        const T apq = cur[p * ld + q], t = cs[3 * k + 2];
+                        nxt[p * ld + p] = cur[p * ld + p] - t * apq;
+                        nxt[q * ld + q] = cur[q * ld + q] + t * apq;
+                        nxt[p * ld + q] = T(0);
+                        nxt[q * ld + p] = T(0);
+                    } else {
+                        nxt[p * ld + p] = cur[p * ld + p];
+                    }
+                    continue;
+                }
+                const T ck = cs[3 * k], sk = cs[3 * k + 1], cl = cs[3 * l], sl = cs[3 * l + 1];
+                const bool qv = q < n, uv = u < n;
+                const T xpr = cur[p * ld + r];
+                const T xpu = uv ? cur[p * ld + u] : T(0);
+                const T xqr = qv ? cur[q * ld + r] : T(0);
+                const T xqu = (qv && uv) ? cur[q * ld + u] : T(0);
+                const T ypr = ck * xpr - sk * xqr, yqr = sk * xpr + ck * xqr;
+                const T ypu = ck * xpu - sk * xqu, yqu = sk * xpu + ck * xqu;
+                nxt[p * ld + r] = cl * ypr - sl * ypu;
+                if (uv) nxt[p * ld + u] = sl * ypr + cl * ypu;
+                if (qv) nxt[q * ld + r] = cl * yqr - sl * yqu;
+                if (qv && uv) nxt[q * ld + u] = sl * yqr + cl * yqu;
+            }
+            for (int e = tid; e < n * np; e += nt) {
+                const int i = e / np, k = e % np;
+                const int p = pairs[2 * k], q = pairs[2 * k + 1];
+                if (q >= n) continue;
+                const T c = cs[3 * k], sn = cs[3 * k + 1];
+                const T vp = V[i * ld + p], vq = V[i * ld + q];
+                V[i * ld + p] = c * vp - sn * vq;
+                V[i * ld + q] = sn * vp + c * vq;
+            }
+            __syncthreads();
+            T* t = cur; cur = nxt; nxt = t;
+        }
+        if (!__syncthreads_or(rotated)) break;
+    }
+    __syncthreads();
+    return cur;
 }
 
 }  // namespace rtr

@@ -632,11 +632,14 @@ __global__ void sqdiff_kernel(const T* __restrict__ P, const double* __restrict_
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// one CTA: e2 = sum of the partials (block_sum's fixed order), then the RSE
 __global__ void rse_final_kernel(const double* __restrict__ part, int nparts, const double* __restrict__ normX2,
                                  const double* __restrict__ normP2, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double e2 = 0.0;
-        for (int i = 0; i < nparts; ++i) e2 += part[i];
+    __shared__ double red[32];
+    double e2 = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) e2 += part[i];
+    e2 = rtr::block_sum(e2, red);
+    if (threadIdx.x == 0) {
         const double x2 = *normX2;
         *out = sqrt(fmax(x2 - *normP2 + e2, 0.0) / x2);
     }
@@ -1023,7 +1026,7 @@ int run_rse(rtr_plan* p, const void* P, const double* const* Z, const int* ranks
     if (is_f64) sqdiff_kernel<double><<<1024, 256, 0, s>>>((const double*)P, dense, p->pnumel, p->partial);
     else sqdiff_kernel<float><<<1024, 256, 0, s>>>((const float*)P, dense, p->pnumel, p->partial);
     RTR_LAUNCH_CHECK("sqdiff_kernel");
-    rse_final_kernel<<<1, 32, 0, s>>>(p->partial, 1024, p->scal + 0, p->scal + 1, out);
+    rse_final_kernel<<<1, 1024, 0, s>>>(p->partial, 1024, p->scal + 0, p->scal + 1, out);
     RTR_LAUNCH_CHECK("rse_final_kernel");
     return RTR_OK;
 }

@@ -53,11 +53,41 @@ __global__ void gram_partial_kernel(OrthJob job, int src_is_q, double* __restric
     }
 }
 
-// One CTA per mode: G = sum of partials, R = chol(G)^T stored in rfac
-// (lower L, row-major K x K).  On failure runs CGS2 on the source and writes
-// Q directly, marking status[mode] = 1.
-__global__ void chol_or_fallback_kernel(OrthJob job, int src_is_q, const double* __restrict__ part,
-                                        int maxchunks, int kk_stride, double* __restrict__ rfac,
+// gsum[mode][i * 64 + j] = sum over chunks of part (the full symmetric Gram),
+// one thread per (i <= j) entry, spread over many CTAs: float64 adds are slow
+// on this part, so the chunk sum runs as four interleaved chains (fixed
+// order: chunk c goes to chain c mod 4, the chains are added pairwise).
+__global__ void gram_sum_kernel(OrthJob job, const double* __restrict__ part, int maxchunks, int kk_stride,
+                                double* __restrict__ gsum) {
+    const int md = blockIdx.y;
+    if (md >= job.nmodes) return;
+    const int I = job.I[md], K = job.K[md];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= K * K) return;
+    const int i = e / K, j = e % K;
+    if (j < i) return;
+    const int nch = (I + RCH - 1) / RCH;
+    const double* src = part + (int64_t)md * maxchunks * kk_stride + e;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int c = 0;
+    for (; c + 4 <= nch; c += 4) {
+        a0 += src[(int64_t)c * kk_stride];
+        a1 += src[(int64_t)(c + 1) * kk_stride];
+        a2 += src[(int64_t)(c + 2) * kk_stride];
+        a3 += src[(int64_t)(c + 3) * kk_stride];
+    }
+    if (c < nch) a0 += src[(int64_t)c * kk_stride];
+    if (c + 1 < nch) a1 += src[(int64_t)(c + 1) * kk_stride];
+    if (c + 2 < nch) a2 += src[(int64_t)(c + 2) * kk_stride];
+    const double g = (a0 + a1) + (a2 + a3);
+    gsum[(int64_t)md * 4096 + i * 64 + j] = g;
+    gsum[(int64_t)md * 4096 + j * 64 + i] = g;
+}
+
+// One CTA per mode: G from gram_sum_kernel (in rfac), R = chol(G)^T written
+// back to rfac (lower L, row-major, leading dimension 64).  On failure runs
+// CGS2 on the source and writes Q directly, marking status[mode] = 1.
+__global__ void chol_or_fallback_kernel(OrthJob job, int src_is_q, double* __restrict__ rfac,
                                         int* __restrict__ status, int* __restrict__ flags) {
     const int md = blockIdx.x;
     const int I = job.I[md], K = job.K[md];
@@ -66,13 +96,9 @@ __global__ void chol_or_fallback_kernel(OrthJob job, int src_is_q, const double*
     __shared__ double G[64 * 65];
     __shared__ double red[32];
     const int ld = 65;
-    const int nch = (I + RCH - 1) / RCH;
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
         const int i = e / K, j = e % K;
-        const int a = min(i, j), b = max(i, j);
-        double s = 0.0;
-        for (int c = 0; c < nch; ++c) s += part[((int64_t)md * maxchunks + c) * kk_stride + a * K + b];
-        G[i * ld + j] = s;
+        G[i * ld + j] = rfac[(int64_t)md * 4096 + i * 64 + j];
     }
     __syncthreads();
     int ok = 1;
@@ -147,27 +173,43 @@ __global__ void chol_or_fallback_kernel(OrthJob job, int src_is_q, const double*
     }
 }
 
-// Q = Y L^-T row by row (forward substitution with the upper factor L^T).
-__global__ void trsm_rows_kernel(OrthJob job, int src_is_q, const double* __restrict__ rfac,
-                                 const int* __restrict__ status) {
+// Q = Y L^-T, one warp per row (forward substitution with the upper factor
+// L^T).  Row q solves q L^T = y: column-oriented, q_k = y_k / L[k][k] and then
+// y_l -= q_k L[l][k] for l > k, with lane t holding y_t and y_{t+32}, so the
+// float64 dependency chain per row is K steps long rather than K^2 / 2.
+constexpr int TRSM_WARPS = 8;
+__global__ void __launch_bounds__(TRSM_WARPS * 32) trsm_rows_kernel(OrthJob job, int src_is_q,
+                                                                   const double* __restrict__ rfac,
+                                                                   const int* __restrict__ status) {
     const int md = blockIdx.y;
     if (md >= job.nmodes || status[md]) return;
     const int I = job.I[md], K = job.K[md];
     const double* Y = src_is_q ? job.Q[md] : job.Y[md];
     double* Q = job.Q[md];
-    __shared__ double L[64 * 64];
-    for (int e = threadIdx.x; e < K * K; e += blockDim.x) L[(e / K) * 64 + e % K] = rfac[(int64_t)md * 4096 + (e / K) * 64 + e % K];
+    __shared__ double Lt[64 * 64];      // Lt[k * 64 + l] = L[l][k]
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const int l = e / K, k = e % K;
+        Lt[k * 64 + l] = rfac[(int64_t)md * 4096 + l * 64 + k];
+    }
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I; i += gridDim.x * blockDim.x) {
-        double y[64];
-        for (int k = 0; k < K; ++k) y[k] = Y[(int64_t)i * K + k];
-        // row q solves q L^T = y  <=>  q_k = (y_k - sum_{l<k} q_l L[k][l]) / L[k][k]
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * TRSM_WARPS + (threadIdx.x >> 5);
+    for (int i = warp; i < I; i += gridDim.x * TRSM_WARPS) {
+        const double* yr = Y + (int64_t)i * K;
+        double y0 = lane < K ? yr[lane] : 0.0;
+        double y1 = lane + 32 < K ? yr[lane + 32] : 0.0;
         for (int k = 0; k < K; ++k) {
-            double v = y[k];
-            for (int l = 0; l < k; ++l) v -= y[l] * L[k * 64 + l];
-            y[k] = v / L[k * 64 + k];
+            const double yk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, k & 31);
+            const double qk = yk / Lt[k * 64 + k];
+            const double* col = Lt + k * 64;
+            if (lane == k) y0 = qk;
+            else if (lane > k) y0 -= qk * col[lane];
+            if (lane + 32 == k) y1 = qk;
+            else if (lane + 32 > k && lane + 32 < K) y1 -= qk * col[lane + 32];
         }
-        for (int k = 0; k < K; ++k) Q[(int64_t)i * K + k] = y[k];
+        double* qr = Q + (int64_t)i * K;
+        if (lane < K) qr[lane] = y0;
+        if (lane + 32 < K) qr[lane + 32] = y1;
     }
 }
 
@@ -188,12 +230,13 @@ __global__ void sumsq_kernel(const T* __restrict__ X, int64_t n, double* __restr
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// *out = sum of part[0 .. n) (one CTA; block_sum's fixed order)
 __global__ void sum_parts_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += part[i];
-        *out = s;
-    }
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = rtr::block_sum(s, red);
+    if (threadIdx.x == 0) *out = s;
 }
 
 }  // namespace
@@ -232,11 +275,13 @@ int launch_orth(rtr_plan* p, const double* const* Y, double* const* Q, cudaStrea
         dim3 g1((unsigned)std::min(maxchunks, 4 * p->num_sms), (unsigned)job.nmodes);
         gram_partial_kernel<<<g1, 256, 0, s>>>(job, src_is_q, part, maxchunks, kk);
         RTR_LAUNCH_CHECK("gram_partial_kernel");
-        chol_or_fallback_kernel<<<job.nmodes, 256, 0, s>>>(job, src_is_q, part, maxchunks, kk, rfac, st,
-                                                            p->flags);
+        dim3 g2(4096 / 256, (unsigned)job.nmodes);
+        gram_sum_kernel<<<g2, 256, 0, s>>>(job, part, maxchunks, kk, rfac);
+        RTR_LAUNCH_CHECK("gram_sum_kernel");
+        chol_or_fallback_kernel<<<job.nmodes, 256, 0, s>>>(job, src_is_q, rfac, st, p->flags);
         RTR_LAUNCH_CHECK("chol_or_fallback_kernel");
-        dim3 g3((unsigned)rtr_ceil_div(maxI, 64), (unsigned)job.nmodes);
-        trsm_rows_kernel<<<g3, 64, 0, s>>>(job, src_is_q, rfac, st);
+        dim3 g3((unsigned)rtr_ceil_div(maxI, TRSM_WARPS), (unsigned)job.nmodes);
+        trsm_rows_kernel<<<g3, TRSM_WARPS * 32, 0, s>>>(job, src_is_q, rfac, st);
         RTR_LAUNCH_CHECK("trsm_rows_kernel");
     }
     return RTR_OK;
@@ -246,7 +291,7 @@ int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts,
     if (is_f64) sumsq_kernel<double><<<nparts, 256, 0, s>>>((const double*)X, n, part);
     else sumsq_kernel<float><<<nparts, 256, 0, s>>>((const float*)X, n, part);
     RTR_LAUNCH_CHECK("sumsq_kernel");
-    sum_parts_kernel<<<1, 32, 0, s>>>(part, nparts, out);
+    sum_parts_kernel<<<1, 1024, 0, s>>>(part, nparts, out);
     RTR_LAUNCH_CHECK("sum_parts_kernel");
     return RTR_OK;
 }

@@ -4,7 +4,8 @@
 // Step k works on the unfolding C_k (rows x cols, row-major float64):
 //   C_0 = P as K_1 x (K_2 ... K_N)
 //   SVD C_k = U S V^T through the Gram matrix of the smaller side (float64,
-//   many CTAs) and its Jacobi eigendecomposition (one CTA, float64);
+//   many CTAs) and its Jacobi eigendecomposition (one CTA, in shared memory
+//   when it fits; float64 for FP64 plans, float32 for the float plans);
 //   rank r_k = smallest r with sqrt(sum_{i>=r} s_i^2) <= threshold (sqrt(2)
 //   delta for k = 0, delta after; delta = tol ||P|| / sqrt(N)), or forced;
 //   core k = U_r reshaped, carry = S_r V_r^T = U_r^T C_k, which is reshaped
@@ -66,16 +67,17 @@ __global__ void __launch_bounds__(1024) eig_kernel(double* __restrict__ G, T* __
     __syncthreads();
     rtr::block_jacobi_eig<T>(A, V, m, m, pairs, cs, 60, sizeof(T) == 8 ? T(1e-30) : T(1e-13));
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < m; ++i) order[i] = i;
-        // insertion sort by decreasing eigenvalue (m is small)
-        for (int i = 1; i < m; ++i) {
-            const int o = order[i];
-            const T v = A[(int64_t)o * m + o];
-            int j = i - 1;
-            while (j >= 0 && A[(int64_t)order[j] * m + order[j]] < v) { order[j + 1] = order[j]; --j; }
-            order[j + 1] = o;
+    // rank sort by decreasing eigenvalue (ties keep index order; NaN last)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const T vi = A[(int64_t)i * m + i];
+        const T ki = isnan(vi) ? -INFINITY : vi;
+        int rk = 0;
+        for (int j = 0; j < m; ++j) {
+            const T vj = A[(int64_t)j * m + j];
+            const T kj = isnan(vj) ? -INFINITY : vj;
+            rk += (kj > ki) || (kj == ki && j < i);
         }
+        order[rk] = i;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = (double)A[(int64_t)order[i] * m + order[i]];
@@ -84,6 +86,52 @@ __global__ void __launch_bounds__(1024) eig_kernel(double* __restrict__ G, T* __
         Vs[e] = (double)V[r * m + order[c]];
     }
 }
+
+// Shared-memory form for m small enough that A (twice) and V fit in shared
+// memory (block_jacobi_eig_db); ld = m | 1 keeps column accesses free of
+// bank conflicts.  Eigenpairs are sorted by decreasing eigenvalue with a
+// parallel rank sort (ties keep index order; NaN sorts last).
+template <typename T>
+__global__ void __launch_bounds__(1024) eig_smem_kernel(const double* __restrict__ G, int m, double* __restrict__ lam,
+                                                        double* __restrict__ Vs, int max_sweeps, T off_tol) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = m | 1;
+    const int np = (m + 1) / 2;
+    T* A0 = reinterpret_cast<T*>(smem_raw);
+    T* A1 = A0 + (size_t)m * ld;
+    T* V = A1 + (size_t)m * ld;
+    T* cs = V + (size_t)m * ld;                                   // 3 np
+    int* pairs = reinterpret_cast<int*>(cs + 3 * np);             // 2 np
+    int* order = pairs + 2 * np;                                  // m
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) A0[(e / m) * ld + e % m] = (T)G[e];
+    __syncthreads();
+    const T* A = rtr::block_jacobi_eig_db<T>(A0, A1, V, m, ld, pairs, cs, max_sweeps, off_tol);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const T vi = A[i * ld + i];
+        const T ki = isnan(vi) ? -INFINITY : vi;
+        int rk = 0;
+        for (int j = 0; j < m; ++j) {
+            const T vj = A[j * ld + j];
+            const T kj = isnan(vj) ? -INFINITY : vj;
+            rk += (kj > ki) || (kj == ki && j < i);
+        }
+        order[rk] = i;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = (double)A[order[i] * ld + order[i]];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m;
+        Vs[e] = (double)V[r * ld + order[c]];
+    }
+}
+
+template <typename T>
+size_t eig_smem_bytes(int m) {
+    const size_t ld = (size_t)(m | 1), np = (size_t)(m + 1) / 2;
+    return sizeof(T) * (3 * (size_t)m * ld + 3 * np) + sizeof(int) * (2 * np + (size_t)m);
+}
+
+constexpr size_t EIG_SMEM_MAX = 227 * 1024;
 
 // rank from the eigenvalue tail: smallest r >= 1 with sum_{i>=r} max(lam_i, 0) <= thr^2
 __global__ void rank_kernel(const double* __restrict__ lam, int m, double thr2, int cap, int* __restrict__ out) {
@@ -117,16 +165,27 @@ __global__ void left_vectors_kernel(const T* __restrict__ Cm, int64_t rows, int6
     }
 }
 
-// carry = U^T C  (r x cols)
+// carry = U^T C  (r x cols).  The sum over rows runs as four interleaved
+// float64 chains (row i to chain i mod 4, chains added pairwise): a single
+// chain is bound by the float64 add latency of this GPU.
 template <typename T>
 __global__ void carry_kernel(const T* __restrict__ Cm, int64_t rows, int64_t cols, const double* __restrict__ U, int r,
                              double* __restrict__ out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)r * cols;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = e / cols, j = e % cols;
-        double s = 0.0;
-        for (int64_t i = 0; i < rows; ++i) s += U[i * r + k] * (double)Cm[i * cols + j];
-        out[e] = s;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t i = 0;
+        for (; i + 4 <= rows; i += 4) {
+            a0 = fma(U[i * r + k], (double)Cm[i * cols + j], a0);
+            a1 = fma(U[(i + 1) * r + k], (double)Cm[(i + 1) * cols + j], a1);
+            a2 = fma(U[(i + 2) * r + k], (double)Cm[(i + 2) * cols + j], a2);
+            a3 = fma(U[(i + 3) * r + k], (double)Cm[(i + 3) * cols + j], a3);
+        }
+        if (i < rows) a0 = fma(U[i * r + k], (double)Cm[i * cols + j], a0);
+        if (i + 1 < rows) a1 = fma(U[(i + 1) * r + k], (double)Cm[(i + 1) * cols + j], a1);
+        if (i + 2 < rows) a2 = fma(U[(i + 2) * r + k], (double)Cm[(i + 2) * cols + j], a2);
+        out[e] = (a0 + a1) + (a2 + a3);
     }
 }
 
@@ -182,7 +241,17 @@ int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, in
     gram_kernel<T><<<gridn((int64_t)m * m * 32), 256, 0, s>>>(Cm, rows, cols, left, w.G);
     RTR_LAUNCH_CHECK("gram_kernel");
     const size_t np = (size_t)(m + 1) / 2 + 1;
-    if (!eig32) {
+    const size_t sm_bytes = eig32 ? eig_smem_bytes<float>(m) : eig_smem_bytes<double>(m);
+    if (sm_bytes <= EIG_SMEM_MAX) {
+        if (eig32)
+            RTR_CUDA(cudaFuncSetAttribute(eig_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm_bytes));
+        else
+            RTR_CUDA(cudaFuncSetAttribute(eig_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm_bytes));
+        if (eig32) eig_smem_kernel<float><<<1, 1024, sm_bytes, s>>>(w.G, m, w.lam, w.Vs, 60, 1e-13f);
+        else eig_smem_kernel<double><<<1, 1024, sm_bytes, s>>>(w.G, m, w.lam, w.Vs, 60, 1e-30);
+    } else if (!eig32) {
         const size_t smem = 2 * np * (sizeof(double) + sizeof(int));
         eig_kernel<double><<<1, 1024, smem, s>>>(w.G, w.G, w.V, m, w.lam, w.Vs, w.iv + 2);
     } else {

@@ -85,6 +85,22 @@ def test_trsvd_forced_ranks_and_fp32():
     assert rel(ot.tr_full(Zg32), ot.tr_full(Zr32)) < 1e-5
 
 
+def test_trsvd_large_gram_side_both_eigen_paths():
+    """A 120-long first mode: the 120 x 120 Gram matrix takes the
+    shared-memory Jacobi in float32 and the global-memory one in float64 (two
+    float64 copies of A and V do not fit in shared memory)."""
+    dims, R = (120, 24, 20), (2, 3, 2)
+    P = noisy_tr(dims, R, 100.0, 43)
+    Zr, rr = orc.tr_svd(P, 1e-3)
+    Zg, rg = gpu_trsvd(P, 1e-3, "fp64", [16] * 3)
+    assert rg == rr
+    assert rel(ot.tr_full(Zg), ot.tr_full(Zr)) < 1e-5
+    P32 = P.astype(np.float32)
+    Zr32, rr32 = orc.tr_svd(P32.astype(np.float64), 1e-3)
+    Zg32, _ = gpu_trsvd(P32, 1e-3, "fp32", [16] * 3, ranks=rr32)
+    assert rel(ot.tr_full(Zg32), ot.tr_full(Zr32)) < 1e-4
+
+
 def test_trsvd_exact_recovery_small_rank():
     # The GPU reads singular values from float64 Gram matrices, whose rounding
     # leaves eigenvalues of about u ||P||^2 in the null space; the rank test
