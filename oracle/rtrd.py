@@ -68,9 +68,12 @@ def bases(X, K, seed, prec="fp64"):
 def default_chain_order(dims, K):
     """Order in which the mode products of step 7 are applied.  The products
     commute (Eq. 3), so the order only changes rounding; the rule is: largest
-    shrink factor I_n/K_n first, ties broken toward the later mode."""
+    shrink factor I_n/K_n first; among equal factors the last mode first, then
+    the others in increasing mode order (after the last mode, the next product
+    then runs over the longest contiguous runs of the intermediate)."""
     Ke = effective_K(dims, K)
-    return sorted(range(len(dims)), key=lambda n: (Ke[n] / dims[n], -n))
+    N = len(dims)
+    return sorted(range(N), key=lambda n: (Ke[n] / dims[n], 0 if n == N - 1 else 1, n))
 
 
 def project(X, Qs, order=None):

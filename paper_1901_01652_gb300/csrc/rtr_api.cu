@@ -98,13 +98,16 @@ int choose_order(rtr_plan* p) {
         }
         return RTR_OK;
     }
-    // largest shrink first (smallest K_n / I_n), ties to the later mode
+    // largest shrink first (smallest K_n / I_n); among equal ratios the last
+    // mode first, then increasing mode order
     int idx[RTR_MAXN];
     for (int n = 0; n < p->N; ++n) idx[n] = n;
+    const int last = p->N - 1;
     std::stable_sort(idx, idx + p->N, [&](int a, int b) {
         const double ra = (double)p->K[a] / (double)p->dims[a], rb = (double)p->K[b] / (double)p->dims[b];
         if (ra != rb) return ra < rb;
-        return a > b;
+        if ((a == last) != (b == last)) return a == last;
+        return a < b;
     });
     for (int n = 0; n < p->N; ++n) p->order[n] = idx[n];
     return RTR_OK;
@@ -116,7 +119,7 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->partial); cudaFree(p->normx_part); cudaFree(p->scal);
     cudaFree(p->chain[0]); cudaFree(p->chain[1]);
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
-    cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws);
+    cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws); cudaFree(p->ttm_q);
     for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
     if (p->als_exec) cudaGraphExecDestroy(p->als_exec);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -316,6 +319,13 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     RTR_TRY(dalloc(&p->flags, 4));
     RTR_TRYC(cudaMemset(p->flags, 0, 4 * sizeof(int)));
     RTR_TRY(dalloc(&p->svd_ws, trsvd_ws_elems(p->pnumel, &p->svd_cbuf, &p->svd_gmax, &p->svd_umax)));
+    {
+        // mode-product Q converted to the compute type: I_n rows of at most 64 values
+        char* q = nullptr;
+        p->ttm_q_bytes = (size_t)maxI * 64 * esz;
+        RTR_TRY(dalloc(&q, p->ttm_q_bytes));
+        p->ttm_q = q;
+    }
     p->tc_ws_bytes = tc_ws_bytes(p);
     if (p->tc_ws_bytes) {
         char* t = nullptr;

@@ -53,6 +53,7 @@ struct rtr_plan {
     void* sub_ws[2] = {nullptr, nullptr}; size_t sub_bytes = 0;  // subchain ping-pong
     int* flags = nullptr;
     void* tc_ws = nullptr;       size_t tc_ws_bytes = 0;       // tensor-core path workspace
+    void* ttm_q = nullptr;       size_t ttm_q_bytes = 0;       // mode-product Q in the compute type
     double* svd_ws = nullptr;    int64_t svd_cbuf = 0, svd_gmax = 0, svd_umax = 0;  // TR-SVD workspace
 };
 

@@ -105,8 +105,9 @@ def test_chain_order_invariance_and_norm_bound():
 
 
 def test_default_chain_order_rule():
-    assert rtrd.default_chain_order((200, 200, 200, 200), [25] * 4) == [3, 2, 1, 0]
-    assert rtrd.default_chain_order((1024, 1024, 256), [60, 60, 30]) == [1, 0, 2]
+    assert rtrd.default_chain_order((200, 200, 200, 200), [25] * 4) == [3, 0, 1, 2]
+    assert rtrd.default_chain_order((1024, 1024, 256), [60, 60, 30]) == [0, 1, 2]
+    assert rtrd.default_chain_order((1024, 1024, 256), [60, 60, 15]) == [2, 0, 1]
     assert rtrd.default_chain_order((60, 50, 3), [15, 25, 5]) == [0, 1, 2]
 
 
