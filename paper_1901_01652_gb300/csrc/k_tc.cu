@@ -418,29 +418,38 @@ __global__ void tc_reduce_kernel(const double* __restrict__ partial, int nparts,
 }
 
 // ---- TMA-fed variant for modes with B > 1 ------------------------------------
-// Same arithmetic as sketch_tc_kernel; X tiles (128 rows x 64 values of the
-// (A, I, B) view, rows a*I + i with pitch B) arrive by 2-D TMA into a staging
-// ring, so the loads are always in flight without holding registers.
-//   warps 0-7   converters (staging fp32 -> bf16 hi/lo operand tiles), then
-//               warps 0-3 drain the 128 x N accumulator
-//   warps 8-15  Omega generators, two groups of four taking alternate chunks
-//               (one Philox4x64-10 call per thread per chunk is the longest
-//               dependent chain of the pipeline)
-//   warp 16     TMA producer (one lane)
-//   warp 17     MMA issuer (one lane)
+// Same arithmetic as sketch_tc_kernel.  A CTA covers up to 256 rows of the
+// (A, I, B) view (rows a*I + i with pitch B) as MT = 1 or 2 M tiles of 128
+// rows that share one Omega tile, so Omega is generated once per chunk of kc
+// consecutive b for all of them.  Ring slot layout (S slots):
+//   [tile 0: 32 KB][tile 1: 32 KB, if MT = 2][B: N x 64 bf16, SW128]
+// Each tile region receives a TMA box (128 rows x kc float32, dense rows) and
+// is then converted IN PLACE into its bf16 operand tiles: hi in the first
+// 16 KB, lo in the second (SW128 K-major, 128 rows x 64).  Every converter
+// reads its pieces of a tile into registers, the converters meet at a named
+// barrier, and only then write, so no value is overwritten before it is read.
+// Without a separate operand ring the whole of shared memory holds staging
+// slots: up to 192 KB of loads in flight per SM.
+//   warps 0-7   converters, then warps 0 .. 4 MT - 1 drain the accumulators
+//   warps 8-11  Omega generators (one Philox4x64-10 call per thread per chunk
+//               for K <= 40; one Omega tile serves both M tiles)
+//   warp 12     TMA producer (one lane)
+//   warp 13     MMA issuer (one lane)
+// (14 warps: at most four per SM sub-partition, so 128 registers a thread)
 constexpr int TM_CONV_WARPS = 8;
-constexpr int TM_RNG_GROUPS = 2;
+constexpr int TM_RNG_GROUPS = 1;
 constexpr int TM_RNG_WARPS = 4 * TM_RNG_GROUPS;
 constexpr int TM_TMA_WARP = TM_CONV_WARPS + TM_RNG_WARPS;
 constexpr int TM_MMA_WARP = TM_TMA_WARP + 1;
 constexpr int TM_NTHREADS = (TM_MMA_WARP + 1) * 32;
 constexpr int TM_CONV_THREADS = TM_CONV_WARPS * 32;
 constexpr int TM_RNG_THREADS = 128;               // threads of one RNG group
-constexpr uint32_t TM_STAGE_X = 128 * 64 * 4;     // fp32 staging tile
+constexpr uint32_t TM_TILE = 32768;               // one tile region: 128 x 64 float32 = hi + lo bf16
+constexpr int TM_MAX_SLOTS = 6;
 
 struct SketchTmaArgs {
     int64_t A, B;
-    int I, K, N, S_st, S_op;
+    int I, K, N, MT, S;
     int kc;                       // chunk width along b: a multiple of 8 dividing B (or 64);
                                   // FP8: 64 or 32 (whole 32-value scale blocks)
     int fp8;                      // 1: block-scaled float8 values, one MMA (no lo part)
@@ -453,43 +462,54 @@ struct SketchTmaArgs {
     int* flags;
 };
 
+// named barrier 1 among the converter threads only
+__device__ __forceinline__ void conv_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(TM_CONV_THREADS) : "memory");
+}
+// the same barrier with an AND vote: every converter thread gets the same
+// answer, so a bounded wait that gave up in one thread ends the loop in all
+// of them (none is left waiting at a later conv_bar)
+__device__ __forceinline__ bool conv_bar_and(bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred pv, pr;\n\tsetp.ne.u32 pv, %1, 0;\n\tbar.red.and.pred pr, 1, %2, pv;\n\t"
+                 "selp.u32 %0, 1, 0, pr;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v), "n"(TM_CONV_THREADS) : "memory");
+    return r != 0;
+}
+
 __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    const SketchTmaArgs p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t* sm = smem_raw + pad;
-    const int S_st = p.S_st, S_op = p.S_op;
+    const int S = p.S, MT = p.MT;
     const uint32_t b_bytes = (uint32_t)p.N * 128u;
-    const uint32_t op_bytes = 2 * MTILE_BYTES + b_bytes;
-    const uint32_t st0 = smem_u32(sm);
-    const uint32_t op0 = st0 + S_st * TM_STAGE_X;
-    uint16_t* tab = reinterpret_cast<uint16_t*>(sm + S_st * TM_STAGE_X + S_op * op_bytes);
+    const uint32_t slot_bytes = (uint32_t)MT * TM_TILE + b_bytes;
+    const uint32_t sl0 = smem_u32(sm);
+    uint16_t* tab = reinterpret_cast<uint16_t*>(sm + (size_t)S * slot_bytes);
     uint64_t* bars = reinterpret_cast<uint64_t*>(tab + 4096);
-    uint64_t* stfull = bars;
-    uint64_t* stempty = bars + S_st;
-    uint64_t* fullA = bars + 2 * S_st;
-    uint64_t* fullB = fullA + S_op;
-    uint64_t* empty = fullB + S_op;
-    uint64_t* accf = empty + S_op;
+    uint64_t* full = bars;                 // TMA landed (transaction bytes)
+    uint64_t* conv = bars + S;             // operand tiles written (8 converter warps)
+    uint64_t* fullB = bars + 2 * S;        // Omega tile written (4 generator warps)
+    uint64_t* empty = bars + 3 * S;        // MMAs of the slot done (tcgen05.commit)
+    uint64_t* accf = bars + 4 * S;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     double* nred = reinterpret_cast<double*>(accf + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t ncols = (uint32_t)p.N;
+    const uint32_t ncols = (uint32_t)(p.N * MT);
 
-    for (uint32_t off = tid * 16u; off < (uint32_t)S_op * op_bytes; off += TM_NTHREADS * 16u)
-        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(op0 + off), "r"(0) : "memory");
+    // zero every slot once: the Omega tiles' columns kc .. 63 are never written
+    for (uint32_t off = tid * 16u; off < (uint32_t)S * slot_bytes; off += TM_NTHREADS * 16u)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(sl0 + off), "r"(0) : "memory");
     for (int j = tid; j < 4096; j += TM_NTHREADS) tab[j] = p.tab[j];
     if (tid == 0) {
         // one arrival per warp (lane 0 after __syncwarp): same-address
         // arrivals from every thread serialise on the barrier word
-        for (int s = 0; s < S_st; ++s) {
-            mbar_init(&stfull[s], 1);
-            mbar_init(&stempty[s], TM_CONV_WARPS);
-        }
-        for (int s = 0; s < S_op; ++s) {
-            mbar_init(&fullA[s], TM_CONV_WARPS);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], TM_CONV_WARPS);
             mbar_init(&fullB[s], TM_RNG_THREADS / 32);
             mbar_init(&empty[s], 1);
         }
@@ -503,90 +523,103 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int rbeg = blockIdx.y * 128;
-    const int rows_valid = min(128, p.I - rbeg);
+    const int rbeg = blockIdx.y * 256;
+    const int rows_valid = min(128 * MT, p.I - rbeg);
     const int64_t nloc = (blockIdx.x < p.nchunks) ? (p.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int ksteps = (p.kc + 15) >> 4;          // operand columns kc .. 16 ksteps - 1 are written as zeros
     double nsum = 0.0;
 
     if (warp < TM_CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
         const bool want_norm = p.normp != nullptr;
-        Ring rs(S_st), ro(S_op);
-        for (int64_t t = 0; t < nloc; ++t, rs.step(1), ro.step(1)) {
-            const int ss = rs.slot, so = ro.slot;
-            const uint32_t us = rs.use, uo = ro.use;
-            if (!mbar_wait(&stfull[ss], us & 1, abort, p.flags)) break;
-            if (t >= S_op && !mbar_wait(&empty[so], (uo - 1) & 1, abort, p.flags)) break;
-            const uint32_t src = st0 + ss * TM_STAGE_X;
-            const uint32_t hi = op0 + so * op_bytes, lo = hi + MTILE_BYTES;
+        Ring r(S);
+        for (int64_t t = 0; t < nloc; ++t, r.step(1)) {
+            const int s = r.slot;
+            const uint32_t u = r.use;
+            if (!conv_bar_and(mbar_wait(&full[s], u & 1, abort, p.flags))) break;
+            const uint32_t slot = sl0 + s * slot_bytes;
             float csum = 0.f;
-            auto piece = [&](const float4 v, int row, int c4, uint32_t off) {
-                // ||X||^2 is accumulated only in the pass that records it
-                if (want_norm && row < rows_valid) csum += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
-                if (p.fp8) {
-                    // a 32-value scale block is 8 consecutive pieces of one row,
-                    // held by 8 consecutive lanes (kc = 32 or 64)
-                    const float m = group_max(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))), 8);
-                    const MxScale sc = mx_scale(m);
-                    st_shared_v2(hi + off, mx_pair(v.x, v.y, sc), mx_pair(v.z, v.w, sc));
-                    return;
-                }
-                uint32_t h0, l0, h1, l1;
-                split2(v.x, v.y, h0, l0);
-                split2(v.z, v.w, h1, l1);
-                st_shared_v2(hi + off, h0, h1);
-                st_shared_v2(lo + off, l0, l1);
-            };
-            if (p.kc == 64) {
-                // 8 float4 pieces per thread: all loads issued before any conversion
-                float4 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int pc = ct + TM_CONV_THREADS * j;
-                    v[j] = ld_shared_f4(src + (uint32_t)(pc >> 4) * 256u + (uint32_t)(pc & 15) * 16u);
-                }
-                // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15;
-                // the swizzle phase (row & 7) is the same for every j
-                const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
-#pragma unroll
-                for (int j = 0; j < 8; ++j) piece(v[j], (ct >> 4) + 16 * j, ct & 15, off0 + 2048u * j);
-            } else {
-                // kc = 4 Q4 with Q4 a compile-time constant: row/column of a piece
-                // by multiply-shift, loads batched like the full-width case
-                auto run = [&](auto q4c) {
-                    constexpr int Q4 = decltype(q4c)::value;
-                    constexpr int NP = (128 * Q4 + TM_CONV_THREADS - 1) / TM_CONV_THREADS;
-                    float4 v[NP];
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        const int pc = ct + TM_CONV_THREADS * j;
-                        if (pc < 128 * Q4)
-                            v[j] = ld_shared_f4(src + (uint32_t)(pc / Q4) * (uint32_t)(16 * Q4) + (uint32_t)(pc % Q4) * 16u);
+            for (int m = 0; m < MT; ++m) {
+                const uint32_t src = slot + m * TM_TILE;
+                const uint32_t hi = src, lo = src + TM_TILE / 2;
+                const int rows_m = min(128, rows_valid - 128 * m);
+                auto piece = [&](const float4 v, uint32_t off) {
+                    if (p.fp8) {
+                        // a 32-value scale block is 8 consecutive pieces of one row,
+                        // held by 8 consecutive lanes (kc = 32 or 64)
+                        const float mx = group_max(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))), 8);
+                        const MxScale sc = mx_scale(mx);
+                        st_shared_v2(hi + off, mx_pair(v.x, v.y, sc), mx_pair(v.z, v.w, sc));
+                        return;
                     }
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        const int pc = ct + TM_CONV_THREADS * j;
-                        if (pc < 128 * Q4) piece(v[j], pc / Q4, pc % Q4, sw128_off(pc / Q4, 4 * (pc % Q4)));
-                    }
+                    uint32_t h0, l0, h1, l1;
+                    split2(v.x, v.y, h0, l0);
+                    split2(v.z, v.w, h1, l1);
+                    st_shared_v2(hi + off, h0, h1);
+                    st_shared_v2(lo + off, l0, l1);
                 };
-                switch (p.kc >> 2) {
-                    case 2: run(std::integral_constant<int, 2>{}); break;
-                    case 4: run(std::integral_constant<int, 4>{}); break;
-                    case 6: run(std::integral_constant<int, 6>{}); break;
-                    case 8: run(std::integral_constant<int, 8>{}); break;
-                    case 10: run(std::integral_constant<int, 10>{}); break;
-                    case 12: run(std::integral_constant<int, 12>{}); break;
-                    default: run(std::integral_constant<int, 14>{}); break;
+                if (p.kc == 64) {
+                    // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15
+                    float4 v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int row = (ct >> 4) + 16 * j;
+                        v[j] = row < rows_m ? ld_shared_f4(src + (uint32_t)row * 256u + (uint32_t)(ct & 15) * 16u)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (want_norm) csum += v[j].x * v[j].x + v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
+                    }
+                    conv_bar();                        // every piece of this tile is in registers
+                    // the swizzle phase (row & 7) is the same for every j
+                    const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) piece(v[j], off0 + 2048u * j);
+                } else {
+                    // kc = 4 Q4 with Q4 a compile-time constant: row/column of a piece
+                    // by multiply-shift; zero columns kc .. 16 ksteps - 1 afterwards
+                    auto run = [&](auto q4c) {
+                        constexpr int Q4 = decltype(q4c)::value;
+                        constexpr int NP = (128 * Q4 + TM_CONV_THREADS - 1) / TM_CONV_THREADS;
+                        float4 v[NP];
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) {
+                            const int pc = ct + TM_CONV_THREADS * j;
+                            const int row = pc / Q4;
+                            v[j] = (pc < 128 * Q4 && row < rows_m)
+                                       ? ld_shared_f4(src + (uint32_t)row * (uint32_t)(16 * Q4) + (uint32_t)(pc % Q4) * 16u)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (want_norm) csum += v[j].x * v[j].x + v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
+                        }
+                        conv_bar();
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) {
+                            const int pc = ct + TM_CONV_THREADS * j;
+                            if (pc < 128 * Q4) piece(v[j], sw128_off(pc / Q4, 4 * (pc % Q4)));
+                        }
+                        constexpr int ZP = (4 * ((4 * Q4 + 15) / 16) - Q4);   // zero pieces per row
+                        if constexpr (ZP > 0) {
+                            for (int pc = ct; pc < 128 * ZP; pc += TM_CONV_THREADS) {
+                                const uint32_t off = sw128_off(pc / ZP, 4 * (Q4 + pc % ZP));
+                                st_shared_v2(hi + off, 0u, 0u);
+                                if (!p.fp8) st_shared_v2(lo + off, 0u, 0u);
+                            }
+                        }
+                    };
+                    switch (p.kc >> 2) {
+                        case 2: run(std::integral_constant<int, 2>{}); break;
+                        case 4: run(std::integral_constant<int, 4>{}); break;
+                        case 6: run(std::integral_constant<int, 6>{}); break;
+                        case 8: run(std::integral_constant<int, 8>{}); break;
+                        case 10: run(std::integral_constant<int, 10>{}); break;
+                        case 12: run(std::integral_constant<int, 12>{}); break;
+                        default: run(std::integral_constant<int, 14>{}); break;
+                    }
                 }
             }
             nsum += (double)csum;
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&fullA[so]);
-                mbar_arrive(&stempty[ss]);
-            }
+            if (lane == 0) mbar_arrive(&conv[s]);
         }
     } else if (warp < TM_TMA_WARP) {
         // ================================================================ Omega generators
@@ -596,16 +629,16 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
         const int nitems = p.kc * ncall;              // <= 64 * 4 = 2 * TM_RNG_THREADS
         const int it0 = rt, it1 = rt + TM_RNG_THREADS;
         const int rr0 = it0 % p.kc, cb0 = it0 / p.kc, rr1 = it1 % p.kc, cb1 = it1 / p.kc;
-        Ring ro(S_op, grp);
+        Ring r(S, grp);
         ChunkPos cp(blockIdx.x + (int64_t)grp * gridDim.x, (int64_t)TM_RNG_GROUPS * gridDim.x, p.nbc);
-        for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS, ro.step(TM_RNG_GROUPS), cp.step()) {
-            const int so = ro.slot;
-            const uint32_t uo = ro.use;
+        for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS, r.step(TM_RNG_GROUPS), cp.step()) {
+            const int s = r.slot;
+            const uint32_t u = r.use;
             const int64_t a = cp.a, b0 = cp.bi * p.kc;
             const int64_t r0 = a * p.B + b0;
             const int len = (int)min((int64_t)p.kc, p.B - b0);
-            if (t >= S_op && !mbar_wait(&empty[so], (uo - 1) & 1, abort, p.flags)) break;
-            const uint32_t bt = op0 + so * op_bytes + 2 * MTILE_BYTES;
+            if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
+            const uint32_t bt = sl0 + s * slot_bytes + (uint32_t)MT * TM_TILE;
             for (int item = it0; item < nitems; item += TM_RNG_THREADS) {
                 const int rr = item == it0 ? rr0 : rr1, cb = item == it0 ? cb0 : cb1;
                 uint64_t w[4] = {0, 0, 0, 0};
@@ -618,44 +651,50 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
             }
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&fullB[so]);
+            if (lane == 0) mbar_arrive(&fullB[s]);
         }
     } else if (warp == TM_TMA_WARP) {
         // ================================================================ TMA producer
         if (lane == 0) {
-            Ring rs(S_st);
+            Ring r(S);
             ChunkPos cp(blockIdx.x, gridDim.x, p.nbc);
-            for (int64_t t = 0; t < nloc; ++t, rs.step(1), cp.step()) {
-                const int ss = rs.slot;
-                const uint32_t us = rs.use;
-                if (t >= S_st && !mbar_wait(&stempty[ss], (us - 1) & 1, abort, p.flags)) break;
+            const uint32_t box_bytes = (uint32_t)(128 * 4 * p.kc);
+            for (int64_t t = 0; t < nloc; ++t, r.step(1), cp.step()) {
+                const int s = r.slot;
+                const uint32_t u = r.use;
+                if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
                 const int64_t a = cp.a, b0 = cp.bi * p.kc;
-                // the full box is always counted: out-of-range rows (i >= I) and
+                // the full boxes are always counted: out-of-range rows (i >= I) and
                 // columns are zero-filled by the TMA unit without memory traffic
-                mbar_arrive_expect_tx(&stfull[ss], (uint32_t)(128 * 4 * p.kc));
-                tma_load_3d(st0 + ss * TM_STAGE_X, &tmap, (int)b0, rbeg, (int)a, &stfull[ss]);
+                mbar_arrive_expect_tx(&full[s], box_bytes * (uint32_t)MT);
+                for (int m = 0; m < MT; ++m)
+                    tma_load_3d(sl0 + s * slot_bytes + m * TM_TILE, &tmap, (int)b0, rbeg + 128 * m, (int)a, &full[s]);
             }
         }
         __syncwarp();
     } else {
         // ================================================================ MMA issuer
         const uint32_t idesc = idesc_bf16_f32(128, p.N);
-        Ring ro(S_op);
-        for (int64_t t = 0; t < nloc; ++t, ro.step(1)) {
-            const int so = ro.slot;
-            const uint32_t uo = ro.use;
-            if (!mbar_wait(&fullA[so], uo & 1, abort, p.flags)) break;
-            if (!mbar_wait(&fullB[so], uo & 1, abort, p.flags)) break;
+        Ring r(S);
+        for (int64_t t = 0; t < nloc; ++t, r.step(1)) {
+            const int s = r.slot;
+            const uint32_t u = r.use;
+            if (!mbar_wait(&conv[s], u & 1, abort, p.flags)) break;
+            if (!mbar_wait(&fullB[s], u & 1, abort, p.flags)) break;
             tc_fence_after();
             if (lane == 0) {
-                const uint32_t ahi = op0 + so * op_bytes, alo = ahi + MTILE_BYTES, bb = ahi + 2 * MTILE_BYTES;
-                const int ksteps = (p.kc + 15) >> 4;      // columns kc..16*ksteps-1 stay zero
-                for (int j = 0; j < ksteps; ++j) {
-                    const uint64_t bd = sdesc_sw128(bb + 32u * j);
-                    mma_bf16(tmem, sdesc_sw128(ahi + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                    if (!p.fp8) mma_bf16(tmem, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
+                const uint32_t slot = sl0 + s * slot_bytes;
+                const uint32_t bb = slot + (uint32_t)MT * TM_TILE;
+                for (int m = 0; m < MT; ++m) {
+                    const uint32_t ahi = slot + m * TM_TILE, alo = ahi + TM_TILE / 2;
+                    const uint32_t d = tmem + (uint32_t)(m * p.N);
+                    for (int j = 0; j < ksteps; ++j) {
+                        const uint64_t bd = sdesc_sw128(bb + 32u * j);
+                        mma_bf16(d, sdesc_sw128(ahi + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
+                        if (!p.fp8) mma_bf16(d, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
+                    }
                 }
-                mma_commit(&empty[so]);
+                mma_commit(&empty[s]);
             }
             __syncwarp();
         }
@@ -664,18 +703,19 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     }
 
     // ==================================================================== epilogue
-    if (warp < 4) {
+    if (warp < 4 * MT) {
         const bool have = nloc > 0;
         bool ok = true;
         if (have) {
             ok = mbar_wait(accf, 0, abort, p.flags);
             tc_fence_after();
         }
-        const int row = 32 * warp + lane;
+        const int m = warp >> 2, q = warp & 3;
+        const int row = 128 * m + 32 * q + lane;
         for (int c0 = 0; c0 < p.N; c0 += 32) {
             float v[32];
             if (have && ok) {
-                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * p.N + c0), v);
             } else {
 #pragma unroll
                 for (int k = 0; k < 32; ++k) v[k] = 0.f;
@@ -754,13 +794,14 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     a.nchunks = A * a.nbc;
     a.seed = p->params.seed; a.mode = n;
     a.tab = a.fp8 ? p->tab_e4m3 : p->tab_bf16; a.flags = p->flags;
-    const size_t fixed = 8192 + 64 * 8 + 2048;
-    const size_t op = 2 * (size_t)MTILE_BYTES + (size_t)a.N * 128;
-    a.S_st = 3;
-    a.S_op = (int)std::min<size_t>(3, (SMEM_LIMIT - fixed - 3 * (size_t)TM_STAGE_X) / op);
-    if (a.S_op < 2) { a.S_st = 2; a.S_op = (int)std::min<size_t>(3, (SMEM_LIMIT - fixed - 2 * (size_t)TM_STAGE_X) / op); }
-    const size_t smem = fixed + (size_t)a.S_st * TM_STAGE_X + (size_t)a.S_op * op;
-    const int gy = (int)rtr_ceil_div(I, 128);
+    // a CTA covers up to 256 rows: MT = 2 tiles of 128 when the view has more than 128
+    a.MT = I > 128 ? 2 : 1;
+    const size_t slot = (size_t)a.MT * TM_TILE + (size_t)a.N * 128;
+    const size_t fixed = 8192 + (4 * TM_MAX_SLOTS + 2) * 8 + 64 + 1024;   // table, barriers, scalars, alignment
+    a.S = (int)std::min<size_t>(TM_MAX_SLOTS, (SMEM_LIMIT - fixed) / slot);
+    if (a.S < 2) return rtr_set_error(RTR_EUNSUPPORTED, "TMA sketch: no two slots fit in shared memory");
+    const size_t smem = fixed + (size_t)a.S * slot;
+    const int gy = (int)rtr_ceil_div(I, 256);
     int64_t gx = std::max<int64_t>(1, p->num_sms / gy);
     gx = std::min<int64_t>(gx, a.nchunks);
     if ((size_t)(gx * I * K) > p->partial_elems) return rtr_set_error(RTR_ENOMEM, "sketch partials exceed workspace");
