@@ -897,8 +897,7 @@ namespace {
 
 constexpr int TT_CONV_WARPS = 8;
 constexpr int TT_MMA_WARP = TT_CONV_WARPS;
-constexpr int TT_EPI_WARP0 = TT_CONV_WARPS + 1;
-constexpr int TT_NTHREADS = (TT_CONV_WARPS + 1 + 4) * 32;
+constexpr int TT_NTHREADS = (TT_CONV_WARPS + 1 + 4) * 32;    // converters, MMA issuer, 4 epilogue warps
 constexpr int TT_CONV_THREADS = TT_CONV_WARPS * 32;
 constexpr int TT_PIECES = 128 * 16 / TT_CONV_THREADS;    // float4 pieces per converter thread per unit
 
