@@ -79,7 +79,8 @@ typedef struct {
     double   tol;             /* TR-SVD relative tolerance epsilon */
     int      flags;           /* RTR_PARAM_* bits, 0 = defaults */
     int      chain_order[8];  /* order of the mode products of step 7; all -1 = default
-                                 (largest I_n/K_n first, ties to the later mode) */
+                                 (largest I_n/K_n first; among equal ratios the last
+                                 mode first, then increasing mode order) */
 } rtr_params;
 
 /* Fill *p with defaults: FP32, seed 0, 20 sweeps, tol 1e-2, default chain order. */
@@ -128,7 +129,8 @@ int rtr_sketch(rtr_plan* plan, const void* X, double* const* Y, void* stream);
 
 /*
  * Algorithm 1, steps 6-7 (Eq. 3): Q_n = orth(Y_n) (economy QR with diag(R) > 0,
- * CholeskyQR2 in float64, Householder fallback), then
+ * CholeskyQR2 in float64; a mode whose Cholesky meets a pivot below 1e-14 of
+ * its diagonal falls back to classical Gram-Schmidt applied twice), then
  *     P = X x_{pi_1} Q_{pi_1}^T ... x_{pi_N} Q_{pi_N}^T
  * in the plan's chain order.  Y[n]: I_n x K_n float64 (ignored for modes that
  * are not projected).  Q[n]: I_n x K_n float64 output (identity written for
