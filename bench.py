@@ -216,6 +216,25 @@ def dist_barrier():
         dist.barrier()
 
 
+def max_over_ranks(x, device):
+    """The maximum of x over the ranks of the process group (x itself when
+    there is none): a step's time is the slowest rank's."""
+    if not _DIST["on"]:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def whole_job_gbps(world, bytes_per_rank, steps, ms):
+    """Whole-job throughput in GB/s: every rank's bytes over `steps` steps
+    divided by the max-over-ranks time `ms` (weak scaling: each rank
+    decomposes its own tensor)."""
+    return world * bytes_per_rank * steps / (ms * 1e-3) / 1e9
+
+
 def run_ours(args):
     import torch
     from paper_1901_01652_gb300 import build, rtr
@@ -236,12 +255,7 @@ def run_ours(args):
     rtr.lib()
 
     def dist_max(x):
-        if not _DIST["on"]:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t[0])
+        return max_over_ranks(x, device)
 
     S = args.size
     dims, K, R, sweeps, snr, seed = (S, S, S, S), (25,) * 4, (10,) * 4, 30, 30.0, 1903 + rank
@@ -255,7 +269,7 @@ def run_ours(args):
     sk_ms = phases[0]
     clocks = clk.summary()
     ms_step = ms / args.steps
-    value = world * xbytes * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_gbps(world, xbytes, args.steps, ms)
     torch.cuda.synchronize()
     rse_mixed = float(pipe.eng.rse.cpu()[0])
 
