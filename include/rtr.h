@@ -66,7 +66,7 @@ extern "C" {
 
 /* device flag bits (rtr_plan_flags) */
 #define RTR_FLAG_NONFINITE     1   /* NaN/Inf met in an input or a reduction */
-#define RTR_FLAG_QR_FALLBACK   2   /* CholeskyQR2 failed; Householder QR used */
+#define RTR_FLAG_QR_FALLBACK   2   /* CholeskyQR2 failed; Gram-Schmidt applied twice used */
 #define RTR_FLAG_GRAM_PINV     4   /* an ALS Gram matrix was not SPD; pseudo-inverse used */
 #define RTR_FLAG_TIMEOUT       8   /* a bounded device wait gave up */
 
