@@ -183,6 +183,24 @@ def split_rank(r):
     return best, r // best
 
 
+def _svd(C):
+    """Thin SVD of C (LAPACK)."""
+    return np.linalg.svd(C, full_matrices=False)
+
+
+def canonical_signs(U, Vt):
+    """Reading for TR-SVD (the paper cites it without stating it): the sign of
+    each singular pair (u_k, v_k) is free, yet through the reshapes between
+    steps (the split r = R_1 R_2 of the first step in particular) it changes
+    which tail the next truncation drops.  The result is made unique by
+    flipping each pair so that the entry of u_k largest in magnitude (the
+    first such entry on ties) is positive."""
+    idx = np.argmax(np.abs(U), axis=0)
+    s = np.sign(U[idx, np.arange(U.shape[1])])
+    s[s == 0] = 1.0
+    return U * s, Vt * s[:, None]
+
+
 def tr_svd(P, eps, ranks=None):
     """TR-SVD [Zhao et al. 2016] with relative tolerance eps on P.
 
@@ -190,6 +208,7 @@ def tr_svd(P, eps, ranks=None):
     splits its rank into R_1 R_2, later steps truncate at delta.  With `ranks`
     (R_1..R_N) given, the ranks are forced instead of chosen ("forced" mode,
     used for parity where a rank decision sits on the threshold).
+    Every SVD's singular pairs take the signs of ``canonical_signs``.
     Guarantees ||P - TR(Z)|| <= eps ||P|| in free mode.
     Returns (cores, ranks).
     """
@@ -198,7 +217,8 @@ def tr_svd(P, eps, ranks=None):
     delta = eps * fro(P) / np.sqrt(N)
     Zs = []
     C = P.reshape(dims[0], -1)
-    U, s, Vt = np.linalg.svd(C, full_matrices=False)
+    U, s, Vt = _svd(C)
+    U, Vt = canonical_signs(U, Vt)
     if ranks is None:
         r = trunc_rank(s, np.sqrt(2.0) * delta)
         R0, R1 = split_rank(r)
@@ -211,7 +231,8 @@ def tr_svd(P, eps, ranks=None):
     C = np.transpose(C, (1, 2, 0))                         # (R1, rest, R0)
     for k in range(1, N - 1):
         C = C.reshape(Rk[k] * dims[k], -1)
-        U, s, Vt = np.linalg.svd(C, full_matrices=False)
+        U, s, Vt = _svd(C)
+        U, Vt = canonical_signs(U, Vt)
         if ranks is None:
             rk = trunc_rank(s, delta)
         else:

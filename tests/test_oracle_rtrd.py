@@ -247,6 +247,45 @@ def test_trsvd_forced_ranks_reproduce_free_ranks():
     assert np.allclose(T.tr_full(Za), T.tr_full(Zb), rtol=1e-13, atol=1e-13)
 
 
+def test_canonical_signs_are_independent_of_the_svd_signs():
+    """Each pair (u_k, v_k) leaves canonical_signs with the same sign whatever
+    sign it came in with, and the product U S Vt is unchanged."""
+    rng = np.random.default_rng(29)
+    M = rng.standard_normal((7, 11))
+    U, s, Vt = np.linalg.svd(M, full_matrices=False)
+    Uc, Vc = rtrd.canonical_signs(U, Vt)
+    D = rng.choice([-1.0, 1.0], size=s.size)
+    Uf, Vf = rtrd.canonical_signs(U * D, Vt * D[:, None])
+    assert np.array_equal(Uf, Uc) and np.array_equal(Vf, Vc)
+    assert np.allclose((Uc * s) @ Vc, M, atol=1e-13)
+    for k in range(s.size):
+        i = int(np.argmax(np.abs(Uc[:, k])))
+        assert Uc[i, k] > 0
+
+
+def test_trsvd_does_not_depend_on_the_svd_signs(monkeypatch):
+    """TR-SVD with every SVD's singular pairs flipped at random gives the same
+    cores: a step that skipped the sign rule would reshape a differently
+    signed carry and truncate a different tail at the next step."""
+    rng = np.random.default_rng(30)
+    S = T.tr_full([rng.standard_normal((r0, i, r1)) for r0, i, r1 in ((2, 9, 3), (3, 8, 2), (2, 7, 2), (2, 6, 2))])
+    P = S + 1e-3 * T.fro(S) / np.sqrt(S.size) * rng.standard_normal(S.shape)
+    Za, ra = rtrd.tr_svd(P, 1e-2)
+    raw = rtrd._svd
+    flips = np.random.default_rng(31)
+
+    def flipped(C):
+        U, s, Vt = raw(C)
+        D = flips.choice([-1.0, 1.0], size=s.size)
+        return U * D, s, Vt * D[:, None]
+
+    monkeypatch.setattr(rtrd, "_svd", flipped)
+    Zb, rb = rtrd.tr_svd(P, 1e-2)
+    assert ra == rb
+    for a, b in zip(Za, Zb):
+        assert np.allclose(a, b, rtol=0, atol=1e-12 * np.abs(a).max())
+
+
 def test_split_rank_reading():
     assert rtrd.split_rank(12) == (3, 4)
     assert rtrd.split_rank(16) == (4, 4)
