@@ -123,7 +123,8 @@ int rtr_plan_flags(rtr_plan* plan, int* flags);
  * of X described at RTR_FP8; they need a 16-byte aligned X and, per projected
  * mode, B % 4 == 0 (B > 1) or I_n % 4 == 0 (B = 1), else RTR_EUNSUPPORTED.
  * Y[n] may be NULL for modes that are not projected.  Also records ||X||_F^2
- * (of X itself, not of its float8 copy) in the plan for rtr_rse.
+ * (of X itself, not of its float8 copy) in the plan for rtr_rse; a NaN or Inf
+ * in X makes that sum non-finite and raises RTR_FLAG_NONFINITE (rtr_plan_flags).
  */
 int rtr_sketch(rtr_plan* plan, const void* X, double* const* Y, void* stream);
 
@@ -213,6 +214,17 @@ int rtr_draw_omega(rtr_plan* plan, int mode, int64_t row0, int64_t nrows, int K,
 
 /* Test support: the Gaussian table of a precision as float64 values (host out[4096]). */
 int rtr_gaussian_table(int prec, double* out);
+
+/*
+ * Test support for the device watchdog (no counterpart in the paper): one
+ * thread waits, with the bounded mbarrier wait every tensor-core kernel of
+ * the library uses, on a barrier that nothing completes, with a limit of
+ * limit_us microseconds (1 .. 2e6) instead of the kernels' 2 s.  The wait
+ * gives up, ORs RTR_FLAG_TIMEOUT into *flags (a caller-owned device int) and
+ * the kernel returns normally, so the context stays usable.  Synchronises
+ * `stream`; returns RTR_ETIMEOUT when the flag was raised, RTR_OK otherwise.
+ */
+int rtr_test_bounded_wait(int limit_us, int* flags, void* stream);
 
 /*
  * Allocation-free sketch of one mode (the paper has no counterpart; this is a

@@ -64,6 +64,20 @@ def tr_full(cores):
     return np.trace(T, axis1=0, axis2=-1)
 
 
+def tr_full_unfolded(cores):
+    """Psi([G_n]) through Eq. 2 for tensors too large for ``tr_full``'s
+    open-index contraction (which holds R_1^2 |X| values): with n the longest
+    mode, X_<n> = G_{n,(2)} G_{!=n,<2>}^T as one matrix product, then the
+    cyclic mode order of X_<n> undone."""
+    N = len(cores)
+    dims = [G.shape[1] for G in cores]
+    n = int(np.argmax(dims))
+    Xn = core_matrix(cores[n]) @ subchain_matrix(cores, n).T
+    perm = cyclic_order(N, n)
+    X = Xn.reshape([dims[m] for m in perm])
+    return np.ascontiguousarray(np.transpose(X, np.argsort(perm)))
+
+
 def cyclic_order(N, n):
     """Mode order n, n+1, ..., N-1, 0, ..., n-1 of the TR unfolding X_<n>."""
     return [(n + m) % N for m in range(N)]

@@ -752,7 +752,7 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
         if (p->R[n] * p->R[(n + 1) % N] > 144)
             return rtr_set_error(RTR_EUNSUPPORTED, "TR-ALS: R_%d R_%d = %d > 144", n, (n + 1) % N,
                                  p->R[n] * p->R[(n + 1) % N]);
-    int st = launch_sumsq(P, is_f64, p->pnumel, p->partial, 1024, normP2, s);
+    int st = launch_sumsq(P, is_f64, p->pnumel, p->partial, 1024, normP2, p->flags, s);
     if (st) return st;
 
     auto transfer = [&](int m) -> int {
@@ -1022,7 +1022,7 @@ int run_rse(rtr_plan* p, const void* P, const double* const* Z, const int* ranks
     int st = run_reconstruct(N, Kd, R, Z, RTR_FP64, dense, work, p->sub_bytes * 2, s);
     if (st) return st;
     const int is_f64 = p->params.prec == RTR_FP64;
-    if ((st = launch_sumsq(P, is_f64, p->pnumel, p->partial, 1024, p->scal + 1, s))) return st;
+    if ((st = launch_sumsq(P, is_f64, p->pnumel, p->partial, 1024, p->scal + 1, p->flags, s))) return st;
     if (is_f64) sqdiff_kernel<double><<<1024, 256, 0, s>>>((const double*)P, dense, p->pnumel, p->partial);
     else sqdiff_kernel<float><<<1024, 256, 0, s>>>((const float*)P, dense, p->pnumel, p->partial);
     RTR_LAUNCH_CHECK("sqdiff_kernel");

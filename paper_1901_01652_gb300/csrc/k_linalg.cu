@@ -230,13 +230,18 @@ __global__ void sumsq_kernel(const T* __restrict__ X, int64_t n, double* __restr
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// *out = sum of part[0 .. n) (one CTA; block_sum's fixed order)
-__global__ void sum_parts_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+// *out = sum of part[0 .. n) (one CTA; block_sum's fixed order); a
+// non-finite sum raises RTR_FLAG_NONFINITE in *flags when flags is given
+__global__ void sum_parts_kernel(const double* __restrict__ part, int n, double* __restrict__ out,
+                                 int* __restrict__ flags) {
     __shared__ double red[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
     s = rtr::block_sum(s, red);
-    if (threadIdx.x == 0) *out = s;
+    if (threadIdx.x == 0) {
+        *out = s;
+        if (flags && !isfinite(s)) atomicOr(flags, RTR_FLAG_NONFINITE);
+    }
 }
 
 }  // namespace
@@ -287,11 +292,12 @@ int launch_orth(rtr_plan* p, const double* const* Y, double* const* Q, cudaStrea
     return RTR_OK;
 }
 
-int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out, cudaStream_t s) {
+int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out, int* flags,
+                 cudaStream_t s) {
     if (is_f64) sumsq_kernel<double><<<nparts, 256, 0, s>>>((const double*)X, n, part);
     else sumsq_kernel<float><<<nparts, 256, 0, s>>>((const float*)X, n, part);
     RTR_LAUNCH_CHECK("sumsq_kernel");
-    sum_parts_kernel<<<1, 1024, 0, s>>>(part, nparts, out);
+    sum_parts_kernel<<<1, 1024, 0, s>>>(part, nparts, out, flags);
     RTR_LAUNCH_CHECK("sum_parts_kernel");
     return RTR_OK;
 }

@@ -146,10 +146,11 @@ __global__ void __launch_bounds__(NT) contract_kernel(
     }
 }
 
-// Y[e] = sum_p partial[p * count + e], p in order; norm total likewise.
+// Y[e] = sum_p partial[p * count + e], p in order; norm total likewise (a
+// non-finite total raises RTR_FLAG_NONFINITE in *flags when flags is given).
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nparts, int64_t count,
                                        double* __restrict__ Y, const double* __restrict__ normp,
-                                       int nnorm, double* __restrict__ norm_out) {
+                                       int nnorm, double* __restrict__ norm_out, int* __restrict__ flags) {
     // one warp per output: lanes stride over the partials, then a fixed-order
     // butterfly; the result does not depend on timing
     const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -164,7 +165,10 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
         double s = 0.0;
         for (int p = lane; p < nnorm; p += 32) s += normp[p];
         s = rtr::warp_sum(s);
-        if (lane == 0) *norm_out = s;
+        if (lane == 0) {
+            *norm_out = s;
+            if (flags && !isfinite(s)) atomicOr(flags, RTR_FLAG_NONFINITE);
+        }
     }
 }
 
@@ -224,7 +228,8 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
     RTR_LAUNCH_CHECK("contract_kernel");
     const int64_t count = a.I * a.C;
     reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
-        p->partial, (int)gx, count, a.Y, p->normx_part, (int)(gx * sh.gy), want_norm ? a.norm_out : nullptr);
+        p->partial, (int)gx, count, a.Y, p->normx_part, (int)(gx * sh.gy), want_norm ? a.norm_out : nullptr,
+        p->flags);
     RTR_LAUNCH_CHECK("reduce_partials_kernel");
     return RTR_OK;
 }
@@ -282,6 +287,12 @@ struct NoAllocDevice {
     double* tab64 = nullptr;
     float* tab32 = nullptr;
     int num_sms = 0;
+    // CTAs per SM of contract_kernel<T, TM, TK, true> for each shared-memory
+    // size it launches with, found on first use: [float64][TM index][TK
+    // index][log2 NTK], 0 = not yet; attr[float64][TM index][TK index] = 1
+    // once the kernel's shared-memory limit is raised to its largest size
+    int occ[2][4][2][6] = {};
+    int attr[2][4][2] = {};
 };
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[64];
@@ -311,15 +322,43 @@ int noalloc_setup(NoAllocDevice** out) {
     return RTR_OK;
 }
 
+// The kernel's shared memory depends on (T, TM, TK, NTK) only; its limit
+// (set once to the largest size any NTK needs) and its occupancy per size are
+// set up once per device and reused, so that the split-K width, and with it
+// the float64 summation order, is the same on every call of a shape.
 template <typename T, int TM, int TK>
-int launch_noalloc(const NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cudaStream_t s) {
+int noalloc_occupancy(NoAllocDevice& d, int ntk, size_t smem, int* out) {
+    constexpr int ti = TM == 1 ? 0 : TM == 2 ? 1 : TM == 4 ? 2 : 3;
+    constexpr int tk = TK == 4 ? 0 : 1;
+    int lg = 0;
+    while ((1 << lg) < ntk) ++lg;
+    if (lg > 5) return rtr_set_error(RTR_EINVAL, "contraction shape with %d column groups", ntk);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    auto kern = contract_kernel<T, TM, TK, true>;
+    const int f64 = sizeof(T) == 8;
+    if (!d.attr[f64][ti][tk]) {
+        const size_t smem_max = sizeof(T) * ((size_t)RC * (256 + 1) + (size_t)RC * 32 * TK + 4096);
+        RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        d.attr[f64][ti][tk] = 1;
+    }
+    int& o = d.occ[f64][ti][tk][lg];
+    if (o == 0) {
+        int occ = 0;
+        RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+        o = std::max(1, occ);
+    }
+    *out = o;
+    return RTR_OK;
+}
+
+template <typename T, int TM, int TK>
+int launch_noalloc(NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cudaStream_t s) {
     const int KP = sh.NTK * sh.TK;
     const size_t smem = sizeof(T) * ((size_t)RC * (sh.rows + 1) + (size_t)RC * KP + 4096);
     auto kern = contract_kernel<T, TM, TK, true>;
-    RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
-    occ = std::max(1, occ);
+    const int st = noalloc_occupancy<T, TM, TK>(d, sh.NTK, smem, &occ);
+    if (st) return st;
     int64_t nchunks, nbc = 1;
     if (a.B == 1) nchunks = rtr_ceil_div(a.A, RC);
     else { nbc = rtr_ceil_div(a.B, RC); nchunks = a.A * nbc; }
@@ -332,13 +371,13 @@ int launch_noalloc(const NoAllocDevice& d, const ContractArgs& a, const Shape& s
     RTR_LAUNCH_CHECK("contract_kernel (no-alloc)");
     const int64_t count = a.I * a.C;
     reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(d.scratch, (int)gx, count, a.Y,
-                                                                                nullptr, 0, nullptr);
+                                                                                nullptr, 0, nullptr, nullptr);
     RTR_LAUNCH_CHECK("reduce_partials_kernel (no-alloc)");
     return RTR_OK;
 }
 
 template <typename T>
-int dispatch_noalloc(const NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cudaStream_t s) {
+int dispatch_noalloc(NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cudaStream_t s) {
 #define RTR_CASE(tm, tk) if (sh.TM == tm && sh.TK == tk) return launch_noalloc<T, tm, tk>(d, a, sh, s);
     RTR_CASE(1, 4) RTR_CASE(2, 4) RTR_CASE(4, 4) RTR_CASE(8, 4)
     RTR_CASE(1, 8) RTR_CASE(2, 8) RTR_CASE(4, 8) RTR_CASE(8, 8)

@@ -396,9 +396,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
     if (warp == MMA_WARP) tmem_dealloc(tmem, ncols);
 }
 
+// as reduce_partials_kernel: a non-finite norm total raises RTR_FLAG_NONFINITE
 __global__ void tc_reduce_kernel(const double* __restrict__ partial, int nparts, int64_t count,
                                        double* __restrict__ Y, const double* __restrict__ normp,
-                                       int nnorm, double* __restrict__ norm_out) {
+                                       int nnorm, double* __restrict__ norm_out, int* __restrict__ flags) {
     // one warp per output: lanes stride over the partials, then a fixed-order
     // butterfly; the result does not depend on timing
     const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -413,7 +414,10 @@ __global__ void tc_reduce_kernel(const double* __restrict__ partial, int nparts,
         double s = 0.0;
         for (int p = lane; p < nnorm; p += 32) s += normp[p];
         s = rtr::warp_sum(s);
-        if (lane == 0) *norm_out = s;
+        if (lane == 0) {
+            *norm_out = s;
+            if (flags && !isfinite(s)) atomicOr(flags, RTR_FLAG_NONFINITE);
+        }
     }
 }
 
@@ -823,7 +827,8 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     RTR_LAUNCH_CHECK("sketch_tma_kernel");
     const int64_t count = I * K;
     tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(p->partial, (int)gx, count, Y,
-                                                                          p->normx_part, (int)(gx * gy), norm_out);
+                                                                          p->normx_part, (int)(gx * gy), norm_out,
+                                                                          p->flags);
     RTR_LAUNCH_CHECK("tc_reduce_kernel");
     return RTR_OK;
 }
@@ -877,11 +882,12 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
         RTR_LAUNCH_CHECK("sketch_tc_kernel");
         const int64_t count = I * K;
         tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
-            p->partial, (int)gx, count, Y[n], p->normx_part, (int)(gx * gy), norm_done ? nullptr : p->scal + 0);
+            p->partial, (int)gx, count, Y[n], p->normx_part, (int)(gx * gy), norm_done ? nullptr : p->scal + 0,
+            p->flags);
         RTR_LAUNCH_CHECK("tc_reduce_kernel");
         norm_done = true;
     }
-    if (!norm_done) return launch_sumsq(X, 0, p->numel, p->partial, 1024, p->scal + 0, s);
+    if (!norm_done) return launch_sumsq(X, 0, p->numel, p->partial, 1024, p->scal + 0, p->flags, s);
     return RTR_OK;
 }
 
@@ -1126,5 +1132,40 @@ int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, 
     RTR_CUDA(cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ttm_tc_kernel<<<(unsigned)gx, TT_NTHREADS, smem, s>>>(a);
     RTR_LAUNCH_CHECK("ttm_tc_kernel");
+    return RTR_OK;
+}
+
+// ---- test support: a bounded wait that runs out ------------------------------
+namespace {
+
+// One thread waits on a barrier of this CTA that expects one arrival and
+// never gets it; the bounded wait gives up after limit_ns, raises
+// RTR_FLAG_TIMEOUT in *flags, and the kernel returns normally.
+__global__ void expired_wait_kernel(uint64_t limit_ns, int* flags) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        rtr::tc::mbar_init(&bar, 1);
+        rtr::tc::mbar_fence_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) rtr::tc::mbar_wait(&bar, 0, (volatile int*)&abort_flag, flags, limit_ns);
+}
+
+}  // namespace
+
+extern "C" int rtr_test_bounded_wait(int limit_us, int* flags, void* stream) {
+    if (!flags) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    if (limit_us < 1 || limit_us > 2000000)
+        return rtr_set_error(RTR_EINVAL, "wait limit %d us outside [1, 2000000]", limit_us);
+    cudaStream_t s = (cudaStream_t)stream;
+    expired_wait_kernel<<<1, 32, 0, s>>>((uint64_t)limit_us * 1000ull, flags);
+    RTR_LAUNCH_CHECK("expired_wait_kernel");
+    RTR_CUDA(cudaStreamSynchronize(s));
+    int h = 0;
+    RTR_CUDA(cudaMemcpy(&h, flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & RTR_FLAG_TIMEOUT)
+        return rtr_set_error(RTR_ETIMEOUT, "a bounded device wait gave up after %d us", limit_us);
     return RTR_OK;
 }

@@ -3,9 +3,13 @@
 //
 // Step k works on the unfolding C_k (rows x cols, row-major float64):
 //   C_0 = P as K_1 x (K_2 ... K_N)
-//   SVD C_k = U S V^T through the Gram matrix of the smaller side (float64,
-//   many CTAs) and its Jacobi eigendecomposition (one CTA, in shared memory
-//   when it fits; float64 for FP64 plans, float32 for the float plans);
+//   SVD C_k = U S V^T: FP64 plans by a one-sided Jacobi SVD of C_k itself
+//   (float64, one CTA per rotation pair); the float plans through the Gram
+//   matrix of the smaller side (float64, many CTAs) and its float32 Jacobi
+//   eigendecomposition (one CTA, in shared memory when it fits); each pair
+//   (u_k, v_k) signed so that the entry of u_k largest in magnitude is
+//   positive (the result of TR-SVD depends on these signs through the
+//   reshapes between steps);
 //   rank r_k = smallest r with sqrt(sum_{i>=r} s_i^2) <= threshold (sqrt(2)
 //   delta for k = 0, delta after; delta = tol ||P|| / sqrt(N)), or forced;
 //   core k = U_r reshaped, carry = S_r V_r^T = U_r^T C_k, which is reshaped
@@ -133,13 +137,175 @@ size_t eig_smem_bytes(int m) {
 
 constexpr size_t EIG_SMEM_MAX = 227 * 1024;
 
-// rank from the eigenvalue tail: smallest r >= 1 with sum_{i>=r} max(lam_i, 0) <= thr^2
+// ---- one-sided Jacobi SVD (FP64 plans) ---------------------------------------
+// The m vectors w_k of the smaller side (the rows of C when rows <= cols, its
+// columns otherwise), each of length L, are copied to W (m x L row-major) and
+// Jt (m x m) starts as the identity.  A sweep visits every pair once, in
+// m' - 1 rounds of m'/2 disjoint pairs (circle schedule, m' = m rounded up to
+// even; one CTA per pair), and rotates each pair (i, j) so that w_i . w_j = 0
+// (Hestenes), applying the same rotation to rows i, j of Jt.  At convergence
+// the w_k are orthogonal with sigma_k = ||w_k||, and J = Jt^T holds the
+// eigenvectors of the Gram matrix of the smaller side (C C^T or C^T C) for
+// the eigenvalues sigma_k^2, without that Gram matrix being formed: singular
+// values and vectors carry errors of order u ||C|| instead of u ||C||^2.
+template <typename T>
+__global__ void jac_init_kernel(const T* __restrict__ Cm, int64_t rows, int64_t cols, int left, int m, int64_t L,
+                                double* __restrict__ W, double* __restrict__ Jt) {
+    const int64_t nw = (int64_t)m * L, total = nw + (int64_t)m * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < nw) {
+            const int64_t k = e / L, l = e % L;
+            W[e] = (double)(left ? Cm[k * cols + l] : Cm[l * cols + k]);
+        } else {
+            const int64_t f = e - nw;
+            Jt[f] = (f / m == f % m) ? 1.0 : 0.0;
+        }
+    }
+}
+
+// pair p of round t of the circle schedule over mp (even) indices: index 0
+// stays, indices 1..mp-1 turn one place per round
+__device__ __forceinline__ void jac_pair(int mp, int t, int p, int& i, int& j) {
+    const int ring = mp - 1;
+    if (p == 0) {
+        i = 0;
+        j = t % ring + 1;
+    } else {
+        i = (t + p) % ring + 1;
+        j = (t + mp - 1 - p) % ring + 1;
+    }
+}
+
+constexpr int JAC_THREADS = 256;
+
+__global__ void __launch_bounds__(JAC_THREADS) jac_round_kernel(double* __restrict__ W, double* __restrict__ Jt, int m,
+                                                                int64_t L, int mp, int t, double tol,
+                                                                unsigned* __restrict__ nrot) {
+    __shared__ double red[3][JAC_THREADS / 32];
+    __shared__ double cs[2];
+    int i, j;
+    jac_pair(mp, t, blockIdx.x, i, j);
+    if (i >= m || j >= m) return;                      // the odd index out: uniform per CTA
+    double* wi = W + (int64_t)i * L;
+    double* wj = W + (int64_t)j * L;
+    double a = 0.0, b = 0.0, g = 0.0;
+    for (int64_t l = threadIdx.x; l < L; l += JAC_THREADS) {
+        const double x = wi[l], y = wj[l];
+        a = fma(x, x, a);
+        b = fma(y, y, b);
+        g = fma(x, y, g);
+    }
+    a = rtr::warp_sum(a);
+    b = rtr::warp_sum(b);
+    g = rtr::warp_sum(g);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = g; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = g = 0.0;
+        for (int q = 0; q < JAC_THREADS / 32; ++q) { a += red[0][q]; b += red[1][q]; g += red[2][q]; }
+        double c = 1.0, sn = 0.0;
+        if (a > 0.0 && b > 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+            const double z = (b - a) / (2.0 * g);
+            const double tn = copysign(1.0, z) / (fabs(z) + hypot(1.0, z));
+            c = 1.0 / sqrt(1.0 + tn * tn);
+            sn = c * tn;
+            if (sn != 0.0) atomicAdd(nrot, 1u);
+        }
+        cs[0] = c;
+        cs[1] = sn;
+    }
+    __syncthreads();
+    const double c = cs[0], sn = cs[1];
+    if (sn == 0.0) return;
+    for (int64_t l = threadIdx.x; l < L; l += JAC_THREADS) {
+        const double x = wi[l], y = wj[l];
+        wi[l] = c * x - sn * y;
+        wj[l] = sn * x + c * y;
+    }
+    double* ji = Jt + (int64_t)i * m;
+    double* jj = Jt + (int64_t)j * m;
+    for (int l = threadIdx.x; l < m; l += JAC_THREADS) {
+        const double x = ji[l], y = jj[l];
+        ji[l] = c * x - sn * y;
+        jj[l] = sn * x + c * y;
+    }
+}
+
+// lam (decreasing) = ||w_k||^2 and Vs (m x m, eigenvector columns in the same
+// order) from a converged Jacobi; one CTA.  Ties keep index order; NaN last.
+__global__ void __launch_bounds__(1024) jac_finish_kernel(const double* __restrict__ W, const double* __restrict__ Jt,
+                                                          int m, int64_t L, double* __restrict__ lam,
+                                                          double* __restrict__ Vs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* nrm = reinterpret_cast<double*>(smem_raw);         // m
+    int* order = reinterpret_cast<int*>(nrm + m);               // m
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int k = threadIdx.x >> 5; k < m; k += nwarp) {
+        double s = 0.0;
+        for (int64_t l = lane; l < L; l += 32) s = fma(W[(int64_t)k * L + l], W[(int64_t)k * L + l], s);
+        s = rtr::warp_sum(s);
+        if (lane == 0) nrm[k] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double ki = isnan(nrm[i]) ? -INFINITY : nrm[i];
+        int rk = 0;
+        for (int j = 0; j < m; ++j) {
+            const double kj = isnan(nrm[j]) ? -INFINITY : nrm[j];
+            rk += (kj > ki) || (kj == ki && j < i);
+        }
+        order[rk] = i;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = nrm[order[i]];
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+        const int64_t r = e / m, c = e % m;
+        Vs[e] = Jt[(int64_t)order[c] * m + r];
+    }
+}
+
+// Sign rule of the singular pairs (the TR-SVD reading that makes its result
+// unique): column k of U (rows x r) is negated unless its entry largest in
+// magnitude (the first such entry on ties) is positive.  One warp per column;
+// the carry U^T C formed afterwards follows the same signs.
+__global__ void sign_kernel(double* __restrict__ U, int64_t rows, int r) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int k = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); k < r; k += nw) {
+        double best = -1.0;
+        int64_t bi = rows;
+        for (int64_t i = lane; i < rows; i += 32) {
+            const double v = fabs(U[i * r + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (bi < rows && U[bi * r + k] < 0.0)
+            for (int64_t i = lane; i < rows; i += 32) U[i * r + k] = -U[i * r + k];
+    }
+}
+
+constexpr int JAC_MAX_SWEEPS = 40;
+
+// rank from the eigenvalue tail: smallest r >= 1 with sum_{i>=r} max(lam_i, 0)
+// <= thr^2.  The tail is summed from the smallest eigenvalue up (never as the
+// total minus the leading terms, whose cancellation error u ||C||^2 would hide
+// thresholds below sqrt(u) ||C||).
 __global__ void rank_kernel(const double* __restrict__ lam, int m, double thr2, int cap, int* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double tail = 0.0;
-        for (int i = 0; i < m; ++i) tail += fmax(lam[i], 0.0);
-        int r = 0;
-        while (r < m && tail > thr2) { tail -= fmax(lam[r], 0.0); ++r; }
+        int r = m;
+        for (int i = m - 1; i >= 0; --i) {
+            const double t = tail + fmax(lam[i], 0.0);
+            if (!(t <= thr2)) break;
+            tail = t;
+            r = i;
+        }
         r = max(r, 1);
         out[0] = min(r, cap);
         out[1] = r > cap;
@@ -226,18 +392,58 @@ __global__ void sumsq_svd_kernel(const T* __restrict__ X, int64_t n, double* __r
 
 struct SvdWs {
     double *Cbuf0, *Cbuf1, *G, *V, *Vs, *U, *lam;
-    int* iv;           // [0..1] rank, overflow; [2..] order
+    int* iv;           // [0..1] rank, overflow; [2..] order (Gram route) or the Jacobi rotation count
     double* nrm;
+    int jac_notconv = 0;
 };
 
-// one truncated SVD of C (rows x cols); returns rank (host), writes U (rows x r)
-// and the carry (r x cols) into ws
-// eig32: eigendecomposition in float32 (the float plans) instead of float64
+// Jacobi route of svd_step: W in w.G, Jt in w.V, then lam and Vs
+template <typename T>
+int jacobi_eig(const T* Cm, int64_t rows, int64_t cols, int left, int m, SvdWs& w, cudaStream_t s) {
+    const int64_t L = left ? cols : rows;
+    const int mp = m + (m & 1);
+    unsigned* nrot = reinterpret_cast<unsigned*>(w.iv + 2);
+    jac_init_kernel<T><<<gridn((int64_t)m * L + (int64_t)m * m), 256, 0, s>>>(Cm, rows, cols, left, m, L, w.G, w.V);
+    RTR_LAUNCH_CHECK("jac_init_kernel");
+    bool conv = false;
+    for (int sweep = 0; sweep < JAC_MAX_SWEEPS && !conv; ++sweep) {
+        RTR_CUDA(cudaMemsetAsync(nrot, 0, sizeof(unsigned), s));
+        for (int t = 0; t < mp - 1; ++t) {
+            jac_round_kernel<<<mp / 2, JAC_THREADS, 0, s>>>(w.G, w.V, m, L, mp, t, 1e-15, nrot);
+            RTR_LAUNCH_CHECK("jac_round_kernel");
+        }
+        unsigned h = 0;
+        RTR_CUDA(cudaMemcpyAsync(&h, nrot, sizeof(h), cudaMemcpyDeviceToHost, s));
+        RTR_CUDA(cudaStreamSynchronize(s));
+        conv = h == 0;
+    }
+    if (!conv) w.jac_notconv = 1;
+    const size_t smem = (size_t)m * (sizeof(double) + sizeof(int));
+    if (smem > EIG_SMEM_MAX) return rtr_set_error(RTR_EUNSUPPORTED, "TR-SVD: Gram side %d too large", m);
+    RTR_CUDA(cudaFuncSetAttribute(jac_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    jac_finish_kernel<<<1, 1024, smem, s>>>(w.G, w.V, m, L, w.lam, w.Vs);
+    RTR_LAUNCH_CHECK("jac_finish_kernel");
+    return RTR_OK;
+}
+
+template <typename T>
+int svd_vectors(const T* Cm, int64_t rows, int64_t cols, int left, int m, double thr, int forced, int cap, SvdWs& w,
+                int* r_out, int* overflow, cudaStream_t s);
+
+// one truncated SVD of C (rows x cols); returns rank (host), writes U (rows x r,
+// canonical signs) into ws
+// eig32: the float plans: Gram matrix and its eigendecomposition in float32;
+// otherwise (FP64 plans) the one-sided Jacobi SVD
 template <typename T>
 int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, int cap, SvdWs& w, int* r_out,
              int* overflow, bool eig32, cudaStream_t s) {
     const int left = rows <= cols;
     const int m = (int)(left ? rows : cols);
+    if (!eig32) {
+        const int st = jacobi_eig<T>(Cm, rows, cols, left, m, w, s);
+        if (st) return st;
+        return svd_vectors<T>(Cm, rows, cols, left, m, thr, forced, cap, w, r_out, overflow, s);
+    }
     gram_kernel<T><<<gridn((int64_t)m * m * 32), 256, 0, s>>>(Cm, rows, cols, left, w.G);
     RTR_LAUNCH_CHECK("gram_kernel");
     const size_t np = (size_t)(m + 1) / 2 + 1;
@@ -262,6 +468,13 @@ int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, in
         eig_kernel<float><<<1, 1024, smem, s>>>(w.G, A32, V32, m, w.lam, w.Vs, w.iv + 2);
     }
     RTR_LAUNCH_CHECK("eig_kernel");
+    return svd_vectors<T>(Cm, rows, cols, left, m, thr, forced, cap, w, r_out, overflow, s);
+}
+
+// rank decision on lam, then U (rows x r) from Vs with canonical signs
+template <typename T>
+int svd_vectors(const T* Cm, int64_t rows, int64_t cols, int left, int m, double thr, int forced, int cap, SvdWs& w,
+                int* r_out, int* overflow, cudaStream_t s) {
     int r = forced;
     if (forced <= 0) {
         rank_kernel<<<1, 32, 0, s>>>(w.lam, m, thr * thr, std::min(cap, m), w.iv);
@@ -276,6 +489,8 @@ int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, in
     // 64-thread blocks: the float64 dot products spread over every SM
     left_vectors_kernel<T><<<gridn(rows * r, 64), 64, 0, s>>>(Cm, rows, cols, left, w.Vs, w.lam, m, r, w.U);
     RTR_LAUNCH_CHECK("left_vectors_kernel");
+    sign_kernel<<<gridn((int64_t)r * 32), 256, 0, s>>>(w.U, rows, r);
+    RTR_LAUNCH_CHECK("sign_kernel");
     *r_out = r;
     return RTR_OK;
 }
@@ -362,6 +577,9 @@ int trsvd_impl(rtr_plan* p, const T* P, double tol, double* const* Z, int* ranks
     for (int n = 0; n < N; ++n) ranks[n] = R[n];
     if (overflow)
         return rtr_set_error(RTR_ENOTCONV, "TR-SVD: a chosen rank exceeded the plan's core capacity and was capped");
+    if (w.jac_notconv)
+        return rtr_set_error(RTR_ENOTCONV, "TR-SVD: a Jacobi SVD stopped after %d sweeps before every pair was "
+                             "orthogonal to 1e-15", JAC_MAX_SWEEPS);
     return RTR_OK;
 }
 

@@ -382,7 +382,7 @@ int rtr_sketch(rtr_plan* p, const void* X, double* const* Y, void* stream) {
         if (st) return st;
         norm_done = true;
     }
-    if (!norm_done) return launch_sumsq(X, f64, p->numel, p->partial, 1024, p->scal + 0, s);
+    if (!norm_done) return launch_sumsq(X, f64, p->numel, p->partial, 1024, p->scal + 0, p->flags, s);
     return RTR_OK;
 }
 

@@ -104,7 +104,9 @@ int launch_ttm(rtr_plan* p, int is_f64, const void* X, int64_t A, int64_t I, int
 
 // k_linalg.cu
 int launch_orth(rtr_plan* p, const double* const* Y, double* const* Q, cudaStream_t s);
-int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out,
+// *out = sum of squares of X[0 .. n); a non-finite result raises
+// RTR_FLAG_NONFINITE in *flags (when flags is not NULL)
+int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out, int* flags,
                  cudaStream_t s);
 
 // k_als.cu

@@ -42,12 +42,13 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// Bounded wait: gives up after ~2 s of wall time, raising *abort and the
-// device flag, so that a lost arrival can never hang the GPU.  The global
-// timer is read only every 256 unsuccessful polls (the first read starts the
-// clock): a timer read on every short wait sits on the pipeline's critical
-// path, once per hand-off.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* flags) {
+// Bounded wait: gives up after limit_ns of wall time (2 s unless a caller asks
+// for less), raising *abort and the device flag, so that a lost arrival can
+// never hang the GPU.  The global timer is read only every 256 unsuccessful
+// polls (the first read starts the clock): a timer read on every short wait
+// sits on the pipeline's critical path, once per hand-off.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* flags,
+                                          uint64_t limit_ns = 2000000000ull) {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -56,7 +57,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
             const uint64_t now = globaltimer();
             if (t0 == 0) {
                 t0 = now;
-            } else if (now - t0 > 2000000000ull) {
+            } else if (now - t0 > limit_ns) {
                 *abort = 1;
                 atomicOr(flags, RTR_FLAG_TIMEOUT);
                 return false;

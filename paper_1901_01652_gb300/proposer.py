@@ -23,7 +23,9 @@ N_IN, N_OUT = 320, 10
 
 def sketch_features(X, seed, out=None, stream=None):
     """Spectrum features (float32 CUDA tensor of 320) of a float32 CUDA tensor
-    X with at most 5 modes."""
+    X with at most 5 modes.  The sketches use the allocation-free entry point,
+    whose static scratch array is shared by every call: calls of this function
+    must not overlap on the GPU (other streams or threads)."""
     dims = tuple(X.shape)
     N = len(dims)
     Ys = []

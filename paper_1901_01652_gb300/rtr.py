@@ -27,7 +27,7 @@ ENTRY_POINTS = (
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
     "rtr_sketch_mode_noalloc", "rtr_batch_create", "rtr_batch_destroy", "rtr_batch_run",
     "rtr_batch_graph_kernels", "rtr_batch_flags", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
-    "rtr_mlp_forward", "rtr_mlp_grad", "rtr_mlp_adam", "rtr_mlp_status", "rtr_propose",
+    "rtr_mlp_forward", "rtr_mlp_grad", "rtr_mlp_adam", "rtr_mlp_status", "rtr_propose", "rtr_test_bounded_wait",
 )
 
 
@@ -93,6 +93,7 @@ def lib():
         "rtr_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP]),
         "rtr_mlp_status": (ctypes.c_int, [_VP, _IP]),
         "rtr_propose": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int, _I64P, ctypes.c_int, _IP, _IP]),
+        "rtr_test_bounded_wait": (ctypes.c_int, [ctypes.c_int, _VP, _VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -276,12 +277,28 @@ def rtr_gaussian_table(prec):
     return np.frombuffer(out, dtype=np.float64).copy()
 
 
+def rtr_test_bounded_wait(limit_us, flags, stream=None):
+    """Test support: a device wait on a barrier nothing completes, bounded by
+    limit_us; returns the status code (RTR_ETIMEOUT expected) without raising."""
+    _dev(flags, torch.int32, "flags")
+    return int(lib().rtr_test_bounded_wait(int(limit_us), _ptr(flags), _stream(stream)))
+
+
 def rtr_sketch_mode_noalloc(prec, X, view, K, seed, mode, Y, stream=None):
-    """Allocation-free one-mode sketch; view = (A, I, B) of X around the mode."""
+    """Allocation-free one-mode sketch; view = (A, I, B) of X around the mode.
+
+    The C entry point cannot see the buffers' sizes, so the view is checked
+    here against X (A*I*B elements) and Y (I*K float64) before any launch.
+    Every call shares the library's one static scratch array: calls must not
+    overlap on the GPU (other streams or threads)."""
     op = PREC[prec] if isinstance(prec, str) else int(prec)
+    A, I, B = (int(v) for v in view)
+    if X.numel() != A * I * B:
+        raise ValueError(f"view {(A, I, B)} does not match X with {X.numel()} elements")
+    if Y.numel() != I * int(K):
+        raise ValueError(f"Y has {Y.numel()} elements, the sketch writes I*K = {I * int(K)}")
     _dev(X, torch.float64 if op == RTR_FP64 else torch.float32, "X")
     _dev(Y, torch.float64, "Y")
-    A, I, B = (int(v) for v in view)
     _check(lib().rtr_sketch_mode_noalloc(op, _ptr(X), A, I, B, int(K), int(seed), int(mode), _ptr(Y),
                                          _stream(stream)))
 

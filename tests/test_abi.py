@@ -122,3 +122,16 @@ def test_batch_create_rejects_bad_arguments_on_host(L):
     p.chain_order[1] = 0
     with pytest.raises(rtr.RtrError):
         rtr.rtr_batch_create([(8, 8, 8)], [(4, 4, 4)], [(2, 2, 2)], p)
+
+
+def test_noalloc_wrapper_refuses_a_view_that_does_not_match_the_buffers():
+    """The C entry point cannot see buffer sizes: the binding checks the view
+    (A, I, B) against X and I*K against Y before any launch."""
+    import torch
+    from paper_1901_01652_gb300 import rtr
+    X = torch.zeros(4, dtype=torch.float32)
+    Y = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="does not match X"):
+        rtr.rtr_sketch_mode_noalloc("fp32", X, (1, 40000, 1), 64, 0, 0, Y)
+    with pytest.raises(ValueError, match="I\\*K"):
+        rtr.rtr_sketch_mode_noalloc("fp32", X, (1, 4, 1), 3, 0, 0, Y)

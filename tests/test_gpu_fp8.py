@@ -127,3 +127,33 @@ def test_rtrsvd_fp8_end_to_end_hsi_shaped():
     # the float8 rounding of X (larger than the 1% noise here) costs some
     # accuracy: measured 0.030 against 0.017 for the unquantised sketch
     assert e8 <= 2.0 * e64
+
+
+def test_fp8_sketch_and_chain_at_the_1024x1024x256_kernel_configurations():
+    """The kernels of the hyperspectral-shaped benchmark (1024 x 1024 x 256,
+    K = (60, 60, 30), chain order (2, 0, 1)) at its own launch configurations,
+    on a 16 x 1024 x 256 tensor: mode 1 (view 16 x 1024 x 256) runs the FP8
+    TMA sketch with eight M tiles and 64-wide chunks, as modes 0 and 1 of the
+    benchmark do (I = 1024); mode 2 runs the last-mode FP8 sketch at I = 256
+    with K = 30; the chain starts with the last mode's product on the tensor
+    cores at I = 256, K = 30."""
+    dims, K, order = (16, 1024, 256), (8, 60, 30), (2, 0, 1)
+    X32 = _scaled_rows(dims, 63)
+    X = X32.astype(np.float64)
+    plan = rtr.rtr_plan_create(dims, K, (4, 4, 4), rtr.make_params("fp8", 1904, 1, 1e-2, order))
+    Xd = torch.from_numpy(X32).cuda()
+    Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") for d, k in zip(plan.dims, plan.K)]
+    rtr.rtr_sketch(plan, Xd, Y)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    Yr = orc.sketch(X, K, 1904, "fp8")
+    for n in range(3):
+        assert rel(Y[n].cpu().numpy(), Yr[n]) < 2e-5, n
+    Yd = [torch.from_numpy(y).cuda() for y in Yr]
+    Q = [torch.zeros((d, k), dtype=torch.float64, device="cuda") for d, k in zip(plan.dims, plan.K)]
+    P = torch.zeros(plan.K, dtype=torch.float32, device="cuda")
+    rtr.rtr_project(plan, Xd, Yd, Q, P)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    Pr = orc.project(X, [orc.orth(y) for y in Yr], order)
+    assert rel(P.cpu().numpy(), Pr) < 3e-5

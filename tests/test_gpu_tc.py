@@ -99,3 +99,38 @@ def test_bf16_chain_vs_oracle(dims, K):
     assert rtr.rtr_plan_flags(plan) == 0
     Pr = orc.project(X, [orc.orth(y) for y in Yr], order)
     assert rel(P.cpu().numpy(), Pr) < 3e-5
+
+
+def test_bf16_sketch_and_chain_at_the_200x4_kernel_configurations():
+    """The kernels of the 200^4 benchmark at its own launch configurations, on
+    a 200 x 8 x 200 x 200 tensor (K = 25; mode 1, I = 8 < K, is kept whole):
+    mode 0 (view 1 x 200 x 320000) runs the TMA sketch with two M tiles and
+    full 64-wide chunks, as modes 0 and 1 of 200^4 do; mode 2 (1600 x 200 x
+    200) runs it with 40-wide chunks, as mode 2 of 200^4 does; mode 3 runs the
+    last-mode sketch at I = 200; the chain starts with the last mode's product
+    on the tensor cores at I = 200, K = 25."""
+    dims, K = (200, 8, 200, 200), (25, 25, 25, 25)
+    X32 = np.random.default_rng(24).standard_normal(dims).astype(np.float32)
+    X = X32.astype(np.float64)
+    order = orc.default_chain_order(dims, K)
+    assert order[0] == 3
+    plan = rtr.rtr_plan_create(dims, K, (10,) * 4, rtr.make_params("bf16", 1903, 3, 1e-2, order))
+    Xd = torch.from_numpy(X32).cuda()
+    Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") if pr else None
+         for d, k, pr in zip(plan.dims, plan.K, plan.projected)]
+    rtr.rtr_sketch(plan, Xd, Y)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    Yr = orc.sketch(X, K, 1903, "bf16")
+    assert Yr[1] is None
+    for n in (0, 2, 3):
+        assert rel(Y[n].cpu().numpy(), Yr[n]) < 2e-5, n
+    # the chain from the oracle's sketches
+    Yd = [None if y is None else torch.from_numpy(y).cuda() for y in Yr]
+    Q = [torch.zeros((d, k), dtype=torch.float64, device="cuda") for d, k in zip(plan.dims, plan.K)]
+    P = torch.zeros(plan.K, dtype=torch.float32, device="cuda")
+    rtr.rtr_project(plan, Xd, Yd, Q, P)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    Pr = orc.project(X, [np.eye(d) if y is None else orc.orth(y) for d, y in zip(dims, Yr)], order)
+    assert rel(P.cpu().numpy(), Pr) < 3e-5

@@ -35,6 +35,19 @@ def test_eq1_bruteforce_equals_tr_full():
         assert np.allclose(T.tr_full_bruteforce(cores), T.tr_full(cores), rtol=1e-13, atol=1e-13)
 
 
+def test_eq2_expansion_equals_eq1_bruteforce():
+    """tr_full_unfolded (Eq. 2, longest mode first, order undone) against the
+    element-by-element trace of Eq. 1, with the longest mode in every place."""
+    for dims, R in (((3, 4, 5), (2, 3, 2)), ((6, 3, 4, 3), (3, 1, 2, 2)), ((2, 3, 7, 4), (2, 2, 3, 1)),
+                    ((2, 3, 4, 5, 2), (1, 2, 2, 3, 2))):
+        rng = np.random.default_rng(4)
+        cores = [rng.standard_normal((R[n], dims[n], R[(n + 1) % len(dims)]))
+                 for n in range(len(dims))]
+        X = T.tr_full_unfolded(cores)
+        assert X.shape == dims and X.flags.c_contiguous
+        assert np.allclose(X, T.tr_full_bruteforce(cores), rtol=1e-13, atol=1e-13)
+
+
 def test_cyclic_shift_of_cores_permutes_modes():
     cores = workloads.tr_cores((3, 4, 5, 2), (2, 3, 2, 4), seed=3)
     X = T.tr_full(cores)
