@@ -94,6 +94,62 @@ def backproject(Zs, Qs):
 
 
 # ----------------------------------------------------------------------------
+# Variants of the projection step (Section 3.2, the remark after Algorithm 1,
+# and the sequential form)
+# ----------------------------------------------------------------------------
+
+def power_iterate(X, n, Y, q):
+    """Power iterations on the sketch of mode n, which the remark after
+    Algorithm 1 names as a way to make the spectrum of the projected unfolding
+    decay faster (citing Halko et al.): q times
+        Y <- X_(n) (X_(n)^T orth(Y)),
+    i.e. Y spans (X_(n) X_(n)^T)^q X_(n) Omega_n in exact arithmetic.
+    Reading: Y is orthonormalised (``orth``) before every application of
+    X_(n) X_(n)^T, which keeps the iteration well conditioned; the Y returned
+    is not orthonormalised (step 6 does that, as for q = 0)."""
+    Xn = unfold(X, n)
+    for _ in range(q):
+        Q = orth(Y)
+        Y = Xn @ (Xn.T @ Q)
+    return Y
+
+
+def sketch_power(X, K, seed, q, prec="fp64"):
+    """Algorithm 1 steps 4-5 followed by q power iterations per mode: [Y_n]
+    (None for modes that are not projected).  The iterations use X itself
+    (for prec="fp8" only the first sketch reads the float8 copy)."""
+    return [None if Y is None else power_iterate(X, n, Y, q) for n, Y in enumerate(sketch(X, K, seed, prec))]
+
+
+def project_sequential(X, K, seed, order=None, prec="fp64"):
+    """Sequential form of the projection step (not the paper's Algorithm 1,
+    whose step 5 sketches every mode from X itself): the modes are taken in
+    `order`, and mode n is sketched from the tensor the earlier modes have
+    already shrunk,
+        Y_n = P_(n) Omega_n,  Q_n = orth(Y_n),  P <- P x_n Q_n^T,
+    with Omega_n drawn as in ``oracle.omega`` (key (seed, n)) with one row per
+    entry of the other modes of the current P (row-major index).  A mode with
+    K_n >= I_n is kept whole (Q_n = I).  Returns (Ys, Qs, P), Ys[n] None for
+    unprojected modes."""
+    N = X.ndim
+    if order is None:
+        order = default_chain_order(X.shape, K)
+    Ys, Qs = [None] * N, [None] * N
+    P = X
+    for n in order:
+        A, I, B = mode_view(P.shape, n)
+        if K[n] >= I:
+            Qs[n] = np.eye(I)
+            continue
+        Om = _omega.omega(seed, n, A * B, K[n], prec)
+        Ps = _mxfp8.quantize_for_mode(P, n) if prec == "fp8" else P
+        Ys[n] = unfold(Ps, n) @ Om
+        Qs[n] = orth(Ys[n])
+        P = mode_product(P, Qs[n].T, n)
+    return Ys, Qs, P
+
+
+# ----------------------------------------------------------------------------
 # TR-ALS (cited by the paper, Algorithm 1 step 9; restated from Eq. 2)
 # ----------------------------------------------------------------------------
 
@@ -261,13 +317,20 @@ def rse_identity(normX2, P, Zs):
 
 
 def rtrd(X, K, R, method="als", seed=0, prec="fp64", sweeps=20, init=None,
-         eps=None, ranks=None, order=None):
-    """Algorithm 1 end to end.  Returns a dict with Y, Q, P, Z, G, errors."""
+         eps=None, ranks=None, order=None, power=0, sequential=False):
+    """Algorithm 1 end to end.  Returns a dict with Y, Q, P, Z, G, errors.
+    power = q > 0 adds q power iterations to every sketch
+    (``power_iterate``); sequential=True takes the sequential projection
+    (``project_sequential``) instead of steps 3-8."""
     dims = X.shape
-    Ys, Qs = bases(X, K, seed, prec)
     if order is None:
         order = default_chain_order(dims, K)
-    P = project(X, Qs, order)
+    if sequential:
+        Ys, Qs, P = project_sequential(X, K, seed, order, prec)
+    else:
+        Ys = sketch_power(X, K, seed, power, prec) if power else sketch(X, K, seed, prec)
+        Qs = [np.eye(X.shape[n]) if Y is None else orth(Y) for n, Y in enumerate(Ys)]
+        P = project(X, Qs, order)
     out = {"Y": Ys, "Q": Qs, "P": P, "order": list(order)}
     if method == "als":
         Zs, errs = tr_als(P, R, sweeps, init=init, seed=seed)
