@@ -81,9 +81,13 @@ typedef struct {
     int      chain_order[8];  /* order of the mode products of step 7; all -1 = default
                                  (largest I_n/K_n first; among equal ratios the last
                                  mode first, then increasing mode order) */
+    int      power_iters;     /* q >= 0 power iterations per sketch (the remark after
+                                 Algorithm 1): rtr_sketch returns Y_n after q times
+                                 Y <- X_(n) (X_(n)^T orth(Y)); 0 = the plain sketch */
 } rtr_params;
 
-/* Fill *p with defaults: FP32, seed 0, 20 sweeps, tol 1e-2, default chain order. */
+/* Fill *p with defaults: FP32, seed 0, 20 sweeps, tol 1e-2, default chain order,
+   no power iterations. */
 void rtr_params_default(rtr_params* p);
 
 /* Message of the last failed call on this host thread ("" if none). */
@@ -125,8 +129,33 @@ int rtr_plan_flags(rtr_plan* plan, int* flags);
  * Y[n] may be NULL for modes that are not projected.  Also records ||X||_F^2
  * (of X itself, not of its float8 copy) in the plan for rtr_rse; a NaN or Inf
  * in X makes that sum non-finite and raises RTR_FLAG_NONFINITE (rtr_plan_flags).
+ *
+ * With params.power_iters = q > 0 (Section 3.2, the remark after Algorithm 1:
+ * power iterations, citing Halko et al.) every projected mode then runs q
+ * times  Q = orth(Y_n);  T = X x_n Q^T;  Y_n = X_(n) T_(n)^T,  i.e. Y_n <-
+ * X_(n) X_(n)^T orth(Y_n), on X itself (also for RTR_FP8): the mode product
+ * of rtr_project (tensor cores for the last mode of BF16/FP8 plans) and the
+ * split-K contraction with a stored operand (float32 SIMT for the float
+ * plans, float64 for RTR_FP64).  Each iteration reads X twice per mode and
+ * uses a plan buffer of max_n |X| K_n / I_n values.
  */
 int rtr_sketch(rtr_plan* plan, const void* X, double* const* Y, void* stream);
+
+/*
+ * Sequential form of Algorithm 1 steps 3-8 (not the paper's: its step 5
+ * sketches every mode from X itself): the modes are taken in the plan's chain
+ * order and mode n is sketched from the tensor the earlier modes have already
+ * shrunk,
+ *     Y_n = P_(n) Omega_n,   Q_n = orth(Y_n),   P <- P x_n Q_n^T,
+ * with Omega_n as in rtr_sketch (key (seed, n)) but with one row per entry of
+ * the other modes of the current P (row-major index).  Outputs as rtr_sketch
+ * (Y) and rtr_project (Q, P); records ||X||^2 for rtr_rse.  X is read twice
+ * (its sketch and its product); every later step reads only intermediates.
+ * power_iters must be 0.  RTR_FP8 plans need every sketched intermediate to
+ * meet the FP8 alignment rule of rtr_sketch, else RTR_EUNSUPPORTED.
+ */
+int rtr_project_sequential(rtr_plan* plan, const void* X, double* const* Y, double* const* Q, void* P,
+                           void* stream);
 
 /*
  * Algorithm 1, steps 6-7 (Eq. 3): Q_n = orth(Y_n) (economy QR with diag(R) > 0,

@@ -12,8 +12,12 @@ from . import rtr
 
 class RTRD:
     def __init__(self, dims, K, R, prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None,
-                 device="cuda"):
-        self.params = rtr.make_params(prec, seed, sweeps, tol, chain_order)
+                 device="cuda", power=0, sequential=False):
+        """power: power iterations per sketch (the remark after Algorithm 1);
+        sequential: the sequential projection (rtr_project_sequential) in place
+        of steps 3-8."""
+        self.params = rtr.make_params(prec, seed, sweeps, tol, chain_order, power)
+        self.sequential = bool(sequential)
         with torch.cuda.device(device):
             self.plan = rtr.rtr_plan_create(dims, K, R, self.params)
         p = self.plan
@@ -57,9 +61,15 @@ class RTRD:
     def compute_rse(self, stream=None):
         rtr.rtr_rse(self.plan, self.P, self.Z, self.rse, self.ranks, stream)
 
+    def project_sequential(self, X, stream=None):
+        rtr.rtr_project_sequential(self.plan, X, self.Y, self.Q, self.P, stream)
+
     def run(self, X, method="als", init=None, ranks=None, stream=None):
-        self.sketch(X, stream)
-        self.project(X, stream)
+        if self.sequential:
+            self.project_sequential(X, stream)
+        else:
+            self.sketch(X, stream)
+            self.project(X, stream)
         if method == "als":
             self.als(init, stream)
         elif method == "svd":

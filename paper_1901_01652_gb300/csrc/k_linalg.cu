@@ -252,9 +252,14 @@ size_t orth_ws_elems(int num_sms, int64_t maxI) {
 }
 
 int launch_orth(rtr_plan* p, const double* const* Y, double* const* Q, cudaStream_t s) {
+    return launch_orth_mask(p, Y, Q, ~0u, s);
+}
+
+int launch_orth_mask(rtr_plan* p, const double* const* Y, double* const* Q, unsigned mask, cudaStream_t s) {
     OrthJob job{};
     int64_t maxI = 1;
     for (int n = 0; n < p->N; ++n) {
+        if (!((mask >> n) & 1u)) continue;
         if (!p->proj[n]) {
             if (!Q[n]) return rtr_set_error(RTR_EINVAL, "Q[%d] is NULL", n);
             identity_kernel<<<64, 256, 0, s>>>(Q[n], (int)p->dims[n]);

@@ -22,7 +22,7 @@ template <typename T, int TM, int TK, bool GEN>
 __global__ void __launch_bounds__(NT) contract_kernel(
     const T* __restrict__ X, int64_t A, int I, int64_t B, int C, int NTK, int rows_cta,
     int64_t nchunks, int64_t nbc, uint64_t seed, int mode, const T* __restrict__ table,
-    const T* __restrict__ M, int64_t ldm, double* __restrict__ partial, double* __restrict__ normp) {
+    const T* __restrict__ M, int64_t ldm, int makb, double* __restrict__ partial, double* __restrict__ normp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int KP = NTK * TK;
     const int NTI = NT / NTK;
@@ -99,6 +99,14 @@ __global__ void __launch_bounds__(NT) contract_kernel(
             for (int e = tid; e < RC * KP; e += NT) {
                 const int k = e % KP;
                 if (k >= ncalls * 20) Ms[e] = T(0);
+            }
+        } else if (makb && B > 1) {
+            // (A, C, B) layout: consecutive threads take consecutive b
+            for (int e = tid; e < RC * KP; e += NT) {
+                const int rr = e % RC, k = e / RC;
+                T v = T(0);
+                if (rr < len && k < C) v = M[(a0 * C + k) * B + b0 + rr];
+                Ms[rr * KP + k] = v;
             }
         } else {
             for (int e = tid; e < RC * KP; e += NT) {
@@ -223,8 +231,8 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
     if (want_norm && (size_t)(gx * sh.gy) > p->normx_part_elems)
         return rtr_set_error(RTR_ENOMEM, "norm partials exceed the plan workspace");
     kern<<<grid, NT, smem, s>>>((const T*)a.X, a.A, (int)a.I, a.B, a.C, sh.NTK, sh.rows, nchunks, nbc,
-                                a.seed, a.mode, (const T*)a.table, (const T*)a.M, a.ldm, p->partial,
-                                want_norm ? p->normx_part : nullptr);
+                                a.seed, a.mode, (const T*)a.table, (const T*)a.M, a.makb ? (int64_t)a.C : a.ldm,
+                                a.makb, p->partial, want_norm ? p->normx_part : nullptr);
     RTR_LAUNCH_CHECK("contract_kernel");
     const int64_t count = a.I * a.C;
     reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
@@ -367,7 +375,7 @@ int launch_noalloc(NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cud
     gx = std::min<int64_t>(gx, (int64_t)(kNoAllocScratchDoubles / (a.I * a.C)));   // >= 1, checked by caller
     dim3 grid((unsigned)gx, (unsigned)sh.gy);
     kern<<<grid, NT, smem, s>>>((const T*)a.X, a.A, (int)a.I, a.B, a.C, sh.NTK, sh.rows, nchunks, nbc, a.seed,
-                                a.mode, (const T*)a.table, nullptr, 0, d.scratch, nullptr);
+                                a.mode, (const T*)a.table, nullptr, 0, 0, d.scratch, nullptr);
     RTR_LAUNCH_CHECK("contract_kernel (no-alloc)");
     const int64_t count = a.I * a.C;
     reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(d.scratch, (int)gx, count, a.Y,

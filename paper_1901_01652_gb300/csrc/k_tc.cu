@@ -835,56 +835,60 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
 
 size_t tc_ws_bytes(const rtr_plan* p) { (void)p; return 0; }
 
+// Tensor-core sketch of one mode of a float32 tensor viewed as (A, I, B)
+// (X itself, or an intermediate of the sequential projection): Y = X_(n) Omega_n.
+// norm_out (may be NULL) receives sum x^2 of the tensor.
+int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
+                          double* norm_out, cudaStream_t s) {
+    const int K = p->K[n];
+    const bool aligned16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    const bool fp8 = p->params.prec == RTR_FP8;
+    if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
+        return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s);
+    // the FP8 form exists in the TMA kernel (B > 1) and in the vectorised
+    // last-mode path of sketch_tc_kernel only
+    if (fp8 && (B > 1 || !aligned16 || I % 4 != 0))
+        return rtr_set_error(RTR_EUNSUPPORTED,
+                             "FP8 sketch of mode %d needs a 16-byte aligned X and %s", n,
+                             B > 1 ? "B % 4 == 0 (TMA path)" : "I_n % 4 == 0");
+    int MT, N, S;
+    size_t smem;
+    if (!sketch_geometry(I, K, &MT, &N, &S, &smem))
+        return rtr_set_error(RTR_EUNSUPPORTED, "tensor-core sketch: no stage fits in shared memory");
+    SketchTCArgs a{};
+    a.X = X; a.A = A; a.B = B; a.I = (int)I; a.K = K; a.N = N; a.MT = MT; a.rows_cta = MT * 128; a.S = S;
+    if (B > 1) { a.nbc = rtr_ceil_div(B, KC); a.nchunks = A * a.nbc; }
+    else { a.nbc = 1; a.nchunks = rtr_ceil_div(A, KC); }
+    a.seed = p->params.seed; a.mode = n;
+    a.vec = aligned16 && ((B > 1) ? (B % 4 == 0) : (I % 4 == 0)) ? 1 : 0;
+    a.fp8 = fp8 ? 1 : 0;
+    a.tab = fp8 ? p->tab_e4m3 : p->tab_bf16;
+    a.flags = p->flags;
+    const int gy = (int)rtr_ceil_div(I, a.rows_cta);
+    int64_t gx = std::max<int64_t>(1, p->num_sms / gy);
+    gx = std::min<int64_t>(gx, a.nchunks);
+    if ((size_t)(gx * I * K) > p->partial_elems) return rtr_set_error(RTR_ENOMEM, "sketch partials exceed workspace");
+    if ((size_t)(gx * gy) > p->normx_part_elems) return rtr_set_error(RTR_ENOMEM, "norm partials exceed workspace");
+    a.partial = p->partial;
+    a.normp = norm_out ? p->normx_part : nullptr;
+    RTR_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    sketch_tc_kernel<<<dim3((unsigned)gx, (unsigned)gy), NTHREADS, smem, s>>>(a);
+    RTR_LAUNCH_CHECK("sketch_tc_kernel");
+    const int64_t count = I * K;
+    tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
+        p->partial, (int)gx, count, Y, p->normx_part, (int)(gx * gy), norm_out, p->flags);
+    RTR_LAUNCH_CHECK("tc_reduce_kernel");
+    return RTR_OK;
+}
+
 int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s) {
     bool norm_done = false;
     for (int n = 0; n < p->N; ++n) {
         if (!p->proj[n]) continue;
         int64_t A, I, B;
         rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
-        const int K = p->K[n];
-        const bool aligned16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-        const bool fp8 = p->params.prec == RTR_FP8;
-        if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder()) {
-            int st = launch_sketch_tma(p, X, A, I, B, n, Y[n], norm_done ? nullptr : p->scal + 0, s);
-            if (st) return st;
-            norm_done = true;
-            continue;
-        }
-        // the FP8 form exists in the TMA kernel (B > 1) and in the vectorised
-        // last-mode path of sketch_tc_kernel only
-        if (fp8 && (B > 1 || !aligned16 || I % 4 != 0))
-            return rtr_set_error(RTR_EUNSUPPORTED,
-                                 "FP8 sketch of mode %d needs a 16-byte aligned X and %s", n,
-                                 B > 1 ? "B % 4 == 0 (TMA path)" : "I_n % 4 == 0");
-        int MT, N, S;
-        size_t smem;
-        if (!sketch_geometry(I, K, &MT, &N, &S, &smem))
-            return rtr_set_error(RTR_EUNSUPPORTED, "tensor-core sketch: no stage fits in shared memory");
-        SketchTCArgs a{};
-        a.X = X; a.A = A; a.B = B; a.I = (int)I; a.K = K; a.N = N; a.MT = MT; a.rows_cta = MT * 128; a.S = S;
-        if (B > 1) { a.nbc = rtr_ceil_div(B, KC); a.nchunks = A * a.nbc; }
-        else { a.nbc = 1; a.nchunks = rtr_ceil_div(A, KC); }
-        a.seed = p->params.seed; a.mode = n;
-        const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-        a.vec = aligned && ((B > 1) ? (B % 4 == 0) : (I % 4 == 0)) ? 1 : 0;
-        a.fp8 = fp8 ? 1 : 0;
-        a.tab = fp8 ? p->tab_e4m3 : p->tab_bf16;
-        a.flags = p->flags;
-        const int gy = (int)rtr_ceil_div(I, a.rows_cta);
-        int64_t gx = std::max<int64_t>(1, p->num_sms / gy);
-        gx = std::min<int64_t>(gx, a.nchunks);
-        if ((size_t)(gx * I * K) > p->partial_elems) return rtr_set_error(RTR_ENOMEM, "sketch partials exceed workspace");
-        if ((size_t)(gx * gy) > p->normx_part_elems) return rtr_set_error(RTR_ENOMEM, "norm partials exceed workspace");
-        a.partial = p->partial;
-        a.normp = norm_done ? nullptr : p->normx_part;
-        RTR_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        sketch_tc_kernel<<<dim3((unsigned)gx, (unsigned)gy), NTHREADS, smem, s>>>(a);
-        RTR_LAUNCH_CHECK("sketch_tc_kernel");
-        const int64_t count = I * K;
-        tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(
-            p->partial, (int)gx, count, Y[n], p->normx_part, (int)(gx * gy), norm_done ? nullptr : p->scal + 0,
-            p->flags);
-        RTR_LAUNCH_CHECK("tc_reduce_kernel");
+        const int st = launch_sketch_tc_mode(p, X, A, I, B, n, Y[n], norm_done ? nullptr : p->scal + 0, s);
+        if (st) return st;
         norm_done = true;
     }
     if (!norm_done) return launch_sumsq(X, 0, p->numel, p->partial, 1024, p->scal + 0, p->flags, s);

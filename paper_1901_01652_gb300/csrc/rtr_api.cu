@@ -12,9 +12,6 @@
 size_t contract_partial_elems(int num_sms, int64_t I, int C);
 size_t contract_norm_elems(int num_sms, int64_t I, int C);
 size_t orth_ws_elems(int num_sms, int64_t maxI);
-int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s);
-int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
-                  cudaStream_t s);
 size_t tc_ws_bytes(const rtr_plan* p);
 size_t trsvd_ws_elems(int64_t pnumel, int64_t* cbuf, int64_t* gmax, int64_t* umax);
 
@@ -120,6 +117,7 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->chain[0]); cudaFree(p->chain[1]);
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
     cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws); cudaFree(p->ttm_q);
+    cudaFree(p->pow_q); cudaFree(p->pow_t);
     for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
     if (p->als_exec) cudaGraphExecDestroy(p->als_exec);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -193,6 +191,8 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
         params->prec != RTR_FP8)
         return rtr_set_error(RTR_EINVAL, "unknown precision %d", params->prec);
     if (params->sweeps < 0) return rtr_set_error(RTR_EINVAL, "sweeps < 0");
+    if (params->power_iters < 0 || params->power_iters > 16)
+        return rtr_set_error(RTR_EINVAL, "power_iters = %d outside [0, 16]", params->power_iters);
     rtr_plan* p = new (std::nothrow) rtr_plan();
     if (!p) return rtr_set_error(RTR_ENOMEM, "host allocation failed");
     p->N = N;
@@ -326,6 +326,17 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
         RTR_TRY(dalloc(&q, p->ttm_q_bytes));
         p->ttm_q = q;
     }
+    if (params->power_iters > 0) {
+        // Q of one mode and T = X x_n Q^T for the largest K_n / I_n
+        size_t tmax = 1;
+        for (int n = 0; n < N; ++n)
+            if (p->proj[n]) tmax = std::max<size_t>(tmax, (size_t)(p->numel / dims[n]) * (size_t)p->K[n]);
+        RTR_TRY(dalloc(&p->pow_q, (size_t)maxI * 64));
+        char* t = nullptr;
+        p->pow_t_bytes = tmax * esz;
+        RTR_TRY(dalloc(&t, p->pow_t_bytes));
+        p->pow_t = t;
+    }
     p->tc_ws_bytes = tc_ws_bytes(p);
     if (p->tc_ws_bytes) {
         char* t = nullptr;
@@ -360,29 +371,127 @@ int rtr_plan_flags(rtr_plan* p, int* flags) {
     return RTR_OK;
 }
 
+namespace {
+
+// Power iterations of rtr_sketch: q times, for every projected mode,
+// Q = orth(Y_n); T = X x_n Q^T (A x K x B); Y_n = X_(n) T_(n)^T.
+int power_iterations(rtr_plan* p, const void* X, double* const* Y, cudaStream_t s) {
+    const int f64 = p->params.prec == RTR_FP64;
+    const bool tc = p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8;
+    for (int it = 0; it < p->params.power_iters; ++it) {
+        for (int n = 0; n < p->N; ++n) {
+            if (!p->proj[n]) continue;
+            int64_t A, I, B;
+            rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
+            const int K = p->K[n];
+            if ((size_t)(A * B) * (size_t)K * (f64 ? 8 : 4) > p->pow_t_bytes)
+                return rtr_set_error(RTR_ENOMEM, "power iteration buffer too small");
+            const double* Yarr[RTR_MAXN] = {};
+            double* Qarr[RTR_MAXN] = {};
+            Yarr[n] = Y[n];
+            Qarr[n] = p->pow_q;
+            int st = launch_orth_mask(p, Yarr, Qarr, 1u << n, s);
+            if (st) return st;
+            st = tc ? launch_ttm_tc(p, (const float*)X, A, I, B, p->pow_q, K, (float*)p->pow_t, s)
+                    : launch_ttm(p, f64, X, A, I, B, p->pow_q, K, p->pow_t, s);
+            if (st) return st;
+            ContractArgs a{};
+            a.X = X; a.A = A; a.I = I; a.B = B; a.C = K;
+            a.gen = 0; a.M = p->pow_t; a.ldm = K; a.makb = 1;
+            a.Y = Y[n]; a.norm_out = nullptr;
+            if ((st = launch_contract(p, f64, a, s))) return st;
+        }
+    }
+    return RTR_OK;
+}
+
+}  // namespace
+
 int rtr_sketch(rtr_plan* p, const void* X, double* const* Y, void* stream) {
     if (!p || !X || !Y) return rtr_set_error(RTR_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     for (int n = 0; n < p->N; ++n)
         if (p->proj[n] && !Y[n]) return rtr_set_error(RTR_EINVAL, "Y[%d] is NULL", n);
-    if (p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8) return launch_sketch_tc(p, (const float*)X, Y, s);
-    const int f64 = p->params.prec == RTR_FP64;
-    bool norm_done = false;
-    for (int n = 0; n < p->N; ++n) {
-        if (!p->proj[n]) continue;
-        ContractArgs a{};
-        int64_t A, I, B;
-        rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
-        a.X = X; a.A = A; a.I = I; a.B = B; a.C = p->K[n];
-        a.gen = 1; a.seed = p->params.seed; a.mode = n;
-        a.table = f64 ? (const void*)p->tab64 : (const void*)p->tab32;
-        a.Y = Y[n];
-        a.norm_out = norm_done ? nullptr : p->scal + 0;
-        int st = launch_contract(p, f64, a, s);
-        if (st) return st;
-        norm_done = true;
+    int st = RTR_OK;
+    if (p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8) {
+        st = launch_sketch_tc(p, (const float*)X, Y, s);
+    } else {
+        const int f64 = p->params.prec == RTR_FP64;
+        bool norm_done = false;
+        for (int n = 0; n < p->N; ++n) {
+            if (!p->proj[n]) continue;
+            ContractArgs a{};
+            int64_t A, I, B;
+            rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
+            a.X = X; a.A = A; a.I = I; a.B = B; a.C = p->K[n];
+            a.gen = 1; a.seed = p->params.seed; a.mode = n;
+            a.table = f64 ? (const void*)p->tab64 : (const void*)p->tab32;
+            a.Y = Y[n];
+            a.norm_out = norm_done ? nullptr : p->scal + 0;
+            st = launch_contract(p, f64, a, s);
+            if (st) return st;
+            norm_done = true;
+        }
+        if (!norm_done) st = launch_sumsq(X, f64, p->numel, p->partial, 1024, p->scal + 0, p->flags, s);
     }
-    if (!norm_done) return launch_sumsq(X, f64, p->numel, p->partial, 1024, p->scal + 0, p->flags, s);
+    if (st) return st;
+    if (p->params.power_iters > 0) return power_iterations(p, X, Y, s);
+    return RTR_OK;
+}
+
+int rtr_project_sequential(rtr_plan* p, const void* X, double* const* Y, double* const* Q, void* P, void* stream) {
+    if (!p || !X || !Y || !Q || !P) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    if (p->params.power_iters != 0)
+        return rtr_set_error(RTR_EINVAL, "the sequential projection takes no power iterations");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int f64 = p->params.prec == RTR_FP64;
+    const bool tc = p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8;
+    const size_t esz = f64 ? 8 : 4;
+    unsigned keep = 0;
+    for (int n = 0; n < p->N; ++n) {
+        if (!Q[n]) return rtr_set_error(RTR_EINVAL, "Q[%d] is NULL", n);
+        if (p->proj[n] && !Y[n]) return rtr_set_error(RTR_EINVAL, "Y[%d] is NULL", n);
+        if (!p->proj[n]) keep |= 1u << n;
+    }
+    int st = RTR_OK;
+    if (keep && (st = launch_orth_mask(p, Y, Q, keep, s))) return st;       // Q_n = I
+    int64_t cd[RTR_MAXN];
+    for (int n = 0; n < p->N; ++n) cd[n] = p->dims[n];
+    int nsteps = 0;
+    for (int i = 0; i < p->N; ++i) if (p->proj[p->order[i]]) ++nsteps;
+    if (nsteps == 0) {
+        RTR_CUDA(cudaMemcpyAsync(P, X, (size_t)p->numel * esz, cudaMemcpyDeviceToDevice, s));
+        return launch_sumsq(X, f64, p->numel, p->partial, 1024, p->scal + 0, p->flags, s);
+    }
+    const void* cur = X;
+    int step = 0;
+    for (int i = 0; i < p->N; ++i) {
+        const int n = p->order[i];
+        if (!p->proj[n]) continue;
+        int64_t A, I, B;
+        rtr_mode_view(p->N, cd, n, &A, &I, &B);
+        // the first sketch reads X itself and records ||X||^2
+        double* norm = step == 0 ? p->scal + 0 : nullptr;
+        if (tc) {
+            st = launch_sketch_tc_mode(p, (const float*)cur, A, I, B, n, Y[n], norm, s);
+        } else {
+            ContractArgs a{};
+            a.X = cur; a.A = A; a.I = I; a.B = B; a.C = p->K[n];
+            a.gen = 1; a.seed = p->params.seed; a.mode = n;
+            a.table = f64 ? (const void*)p->tab64 : (const void*)p->tab32;
+            a.Y = Y[n]; a.norm_out = norm;
+            st = launch_contract(p, f64, a, s);
+        }
+        if (st) return st;
+        if ((st = launch_orth_mask(p, Y, Q, 1u << n, s))) return st;
+        void* out = (step == nsteps - 1) ? P : p->chain[step & 1];
+        if (tc && step == 0) st = launch_ttm_tc(p, (const float*)cur, A, I, B, Q[n], p->K[n], (float*)out, s);
+        else st = launch_ttm(p, f64, cur, A, I, B, Q[n], p->K[n], out, s);
+        if (st) return st;
+        cd[n] = p->K[n];
+        cur = out;
+        ++step;
+    }
     return RTR_OK;
 }
 

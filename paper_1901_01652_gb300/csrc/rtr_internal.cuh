@@ -55,6 +55,10 @@ struct rtr_plan {
     void* tc_ws = nullptr;       size_t tc_ws_bytes = 0;       // tensor-core path workspace
     void* ttm_q = nullptr;       size_t ttm_q_bytes = 0;       // mode-product Q in the compute type
     double* svd_ws = nullptr;    int64_t svd_cbuf = 0, svd_gmax = 0, svd_umax = 0;  // TR-SVD workspace
+    // power iterations: Q of the current mode (I_n x K_n float64) and
+    // T = X x_n Q^T in the compute type (max_n |X| K_n / I_n values)
+    double* pow_q = nullptr;
+    void* pow_t = nullptr;       size_t pow_t_bytes = 0;
 };
 
 // ---- error reporting (rtr_api.cu) -------------------------------------------
@@ -91,8 +95,10 @@ struct ContractArgs {
     int C;
     // generated operand
     int gen; uint64_t seed; int mode; const void* table;
-    // stored operand (gen == 0), same element type as X
-    const void* M; int64_t ldm;
+    // stored operand (gen == 0), same element type as X: row r = a*B + b at
+    // M[r * ldm + c] (makb = 0), or M laid out (A, C, B), entry (a, c, b) at
+    // M[(a * C + c) * B + b] (makb = 1: the output of a mode product)
+    const void* M; int64_t ldm; int makb;
     double* Y;                  // I x C float64 output
     double* norm_out;           // optional: receives sum x^2 (float64) of X
 };
@@ -104,6 +110,8 @@ int launch_ttm(rtr_plan* p, int is_f64, const void* X, int64_t A, int64_t I, int
 
 // k_linalg.cu
 int launch_orth(rtr_plan* p, const double* const* Y, double* const* Q, cudaStream_t s);
+// the modes whose bit is set in `mask` only (Y, Q: arrays of N pointers)
+int launch_orth_mask(rtr_plan* p, const double* const* Y, double* const* Q, unsigned mask, cudaStream_t s);
 // *out = sum of squares of X[0 .. n); a non-finite result raises
 // RTR_FLAG_NONFINITE in *flags (when flags is not NULL)
 int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out, int* flags,
@@ -131,6 +139,15 @@ int batch_als_create(BatchAls** out, int count, int N, const int64_t* K, const i
 void batch_als_destroy(BatchAls* b);
 int batch_als_run(BatchAls* b, double* err, cudaStream_t s);
 int batch_als_flags(BatchAls* b, int* flags);
+
+// k_tc.cu: tensor-core sketch (BF16/FP8 plans) of one mode of a float32
+// tensor viewed as (A, I, B), and of every projected mode of X; the
+// tensor-core product of the last mode (B = 1), other views fall back to launch_ttm
+int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
+                          double* norm_out, cudaStream_t s);
+int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s);
+int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
+                  cudaStream_t s);
 
 // k_trsvd.cu
 int run_trsvd(rtr_plan* p, const void* P, double tol, double* const* Z, int* ranks, cudaStream_t s);

@@ -23,7 +23,7 @@ PARAM_NO_GRAPH = 1
 # every entry point of include/rtr.h
 ENTRY_POINTS = (
     "rtr_params_default", "rtr_last_error", "rtr_kernel_launches", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
-    "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_als", "rtr_svd", "rtr_backproject",
+    "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_project_sequential", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
     "rtr_sketch_mode_noalloc", "rtr_batch_create", "rtr_batch_destroy", "rtr_batch_run",
     "rtr_batch_graph_kernels", "rtr_batch_flags", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
@@ -39,7 +39,8 @@ class RtrError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("sweeps", ctypes.c_int),
-                ("tol", ctypes.c_double), ("flags", ctypes.c_int), ("chain_order", ctypes.c_int * 8)]
+                ("tol", ctypes.c_double), ("flags", ctypes.c_int), ("chain_order", ctypes.c_int * 8),
+                ("power_iters", ctypes.c_int)]
 
 
 _lib = None
@@ -67,6 +68,7 @@ def lib():
         "rtr_plan_flags": (ctypes.c_int, [_VP, _IP]),
         "rtr_sketch": (ctypes.c_int, [_VP, _VP, _VPP, _VP]),
         "rtr_project": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
+        "rtr_project_sequential": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
         "rtr_als": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.c_int, _VP, _VP]),
         "rtr_svd": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VPP, _IP, _VP]),
         "rtr_backproject": (ctypes.c_int, [_VP, _VPP, _VPP, _VPP, _IP, _VP]),
@@ -185,12 +187,13 @@ def rtr_params_default():
     return p
 
 
-def make_params(prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None):
+def make_params(prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None, power=0):
     p = rtr_params_default()
     p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     p.seed = int(seed)
     p.sweeps = int(sweeps)
     p.tol = float(tol)
+    p.power_iters = int(power)
     if chain_order is not None:
         for i, m in enumerate(chain_order):
             p.chain_order[i] = int(m)
@@ -224,6 +227,13 @@ def rtr_project(plan, X, Y, Q, P, stream=None):
     _dev(P, plan.x_dtype, "P")
     _check(lib().rtr_project(plan.handle, _ptr(X), _ptrs(Y, torch.float64, "Y"), _ptrs(Q, torch.float64, "Q"),
                              _ptr(P), _stream(stream)))
+
+
+def rtr_project_sequential(plan, X, Y, Q, P, stream=None):
+    _dev(X, plan.x_dtype, "X")
+    _dev(P, plan.x_dtype, "P")
+    _check(lib().rtr_project_sequential(plan.handle, _ptr(X), _ptrs(Y, torch.float64, "Y"),
+                                        _ptrs(Q, torch.float64, "Q"), _ptr(P), _stream(stream)))
 
 
 def rtr_als(plan, P, Z, init_given, err=None, stream=None):
