@@ -172,6 +172,32 @@ int rtr_project(rtr_plan* plan, const void* X, const double* const* Y,
                 double* const* Q, void* P, void* stream);
 
 /*
+ * Out-of-core form of Algorithm 1 steps 3-8 for a tensor in HOST memory (one
+ * larger than the GPU's, or one that should not be copied whole): X is
+ * streamed to the GPU in slabs of slab_rows indices of mode 0 (contiguous in
+ * row-major order), twice.  Pass 1 sketches every projected mode slab by slab:
+ * a slab holds whole rows of Y_0, and adds its part of Y_n = X_(n) Omega_n for
+ * the other modes, the test-matrix rows counted over the whole tensor, so Y is
+ * rtr_sketch's up to summation order; ||X||^2 is recorded for rtr_rse.  Then
+ * Q_n = orth(Y_n) as in rtr_project, and pass 2 applies every mode product but
+ * mode 0's to each slab and adds the slab's share of the mode-0 product into
+ * P, P = sum over slabs of T_slab x_0 Q_0[slab rows]^T (Eq. 3: the products
+ * commute, and mode 0's splits over its rows).  The plan's chain order must
+ * end with mode 0; power_iters must be 0.
+ * X_host: HOST pointer to X (page-locked memory lets the copies overlap the
+ * kernels); it must stay valid until `stream` has passed this call's work.
+ * stage[2]: caller-owned DEVICE buffers of stage_bytes each, at least
+ * slab_rows * prod_{m>0} I_m elements (float64 for RTR_FP64 plans, float32
+ * otherwise).  The copies run on a stream of the plan, overlapped with the
+ * kernels on `stream` through events.  Y, Q, P as in rtr_sketch and
+ * rtr_project.  RTR_FP8 plans with several slabs need slab_rows x
+ * prod(I_1 .. I_{N-2}) to be a multiple of 32 (whole scale blocks of the last
+ * mode's sketch), else RTR_EUNSUPPORTED.
+ */
+int rtr_project_host(rtr_plan* plan, const void* X_host, int64_t slab_rows, void* const* stage, size_t stage_bytes,
+                     double* const* Y, double* const* Q, void* P, void* stream);
+
+/*
  * Algorithm 1, step 9 with TR-ALS: fit cores Z_n (R_n x K_n x R_{n+1},
  * float64) to P by `sweeps` sweeps of exact least-squares core updates
  * (Eq. 2: P_<n> = Z_{n,(2)} S^T, S the subchain; Z_{n,(2)} = P_<n> S (S^T S)^-1,

@@ -297,6 +297,22 @@ int launch_orth_mask(rtr_plan* p, const double* const* Y, double* const* Q, unsi
     return RTR_OK;
 }
 
+namespace {
+template <typename T>
+__global__ void add_kernel(T* __restrict__ y, const T* __restrict__ x, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] += x[e];
+}
+}  // namespace
+
+int launch_add(void* y, const void* x, int64_t n, int is_f64, cudaStream_t s) {
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(rtr_ceil_div(n, 256), 4096));
+    if (is_f64) add_kernel<double><<<g, 256, 0, s>>>((double*)y, (const double*)x, n);
+    else add_kernel<float><<<g, 256, 0, s>>>((float*)y, (const float*)x, n);
+    RTR_LAUNCH_CHECK("add_kernel");
+    return RTR_OK;
+}
+
 int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out, int* flags,
                  cudaStream_t s) {
     if (is_f64) sumsq_kernel<double><<<nparts, 256, 0, s>>>((const double*)X, n, part);

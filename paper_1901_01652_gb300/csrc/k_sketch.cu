@@ -21,7 +21,7 @@ constexpr int NT = 256;       // threads per CTA
 template <typename T, int TM, int TK, bool GEN>
 __global__ void __launch_bounds__(NT) contract_kernel(
     const T* __restrict__ X, int64_t A, int I, int64_t B, int C, int NTK, int rows_cta,
-    int64_t nchunks, int64_t nbc, uint64_t seed, int mode, const T* __restrict__ table,
+    int64_t nchunks, int64_t nbc, int64_t aoff, uint64_t seed, int mode, const T* __restrict__ table,
     const T* __restrict__ M, int64_t ldm, int makb, double* __restrict__ partial, double* __restrict__ normp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int KP = NTK * TK;
@@ -62,7 +62,10 @@ __global__ void __launch_bounds__(NT) contract_kernel(
             cb += qb; ca += qa;
             if (cb >= nbc) { cb -= nbc; ++ca; }
         }
-        const int64_t rbase = (B == 1) ? a0 : a0 * B + b0;   // r of rr = 0
+        const int64_t rbase = (B == 1) ? a0 : a0 * B + b0;   // r of rr = 0 (stored operand)
+        // generated operand: the row of Omega_n counts a from aoff (a slab of a
+        // larger tensor along its slowest modes)
+        const int64_t gbase = (B == 1) ? a0 + aoff : (a0 + aoff) * B + b0;
         __syncthreads();
         // ---- X tile -> Xs[rr][il]
         if (B == 1) {
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(NT) contract_kernel(
             for (int w = tid; w < RC * ncalls; w += NT) {
                 const int rr = w % RC, cb = w / RC;
                 uint64_t wd[4] = {0, 0, 0, 0};
-                if (rr < len) rtr::omega_words(seed, mode, (uint64_t)(rbase + rr), (uint64_t)cb, wd);
+                if (rr < len) rtr::omega_words(seed, mode, (uint64_t)(gbase + rr), (uint64_t)cb, wd);
 #pragma unroll
                 for (int t = 0; t < 20; ++t) {
                     const int k = cb * 20 + t;
@@ -231,7 +234,7 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
     if (want_norm && (size_t)(gx * sh.gy) > p->normx_part_elems)
         return rtr_set_error(RTR_ENOMEM, "norm partials exceed the plan workspace");
     kern<<<grid, NT, smem, s>>>((const T*)a.X, a.A, (int)a.I, a.B, a.C, sh.NTK, sh.rows, nchunks, nbc,
-                                a.seed, a.mode, (const T*)a.table, (const T*)a.M, a.makb ? (int64_t)a.C : a.ldm,
+                                a.aoff, a.seed, a.mode, (const T*)a.table, (const T*)a.M, a.makb ? (int64_t)a.C : a.ldm,
                                 a.makb, p->partial, want_norm ? p->normx_part : nullptr);
     RTR_LAUNCH_CHECK("contract_kernel");
     const int64_t count = a.I * a.C;
@@ -374,8 +377,8 @@ int launch_noalloc(NoAllocDevice& d, const ContractArgs& a, const Shape& sh, cud
     gx = std::min<int64_t>(gx, nchunks);
     gx = std::min<int64_t>(gx, (int64_t)(kNoAllocScratchDoubles / (a.I * a.C)));   // >= 1, checked by caller
     dim3 grid((unsigned)gx, (unsigned)sh.gy);
-    kern<<<grid, NT, smem, s>>>((const T*)a.X, a.A, (int)a.I, a.B, a.C, sh.NTK, sh.rows, nchunks, nbc, a.seed,
-                                a.mode, (const T*)a.table, nullptr, 0, 0, d.scratch, nullptr);
+    kern<<<grid, NT, smem, s>>>((const T*)a.X, a.A, (int)a.I, a.B, a.C, sh.NTK, sh.rows, nchunks, nbc, (int64_t)0,
+                                a.seed, a.mode, (const T*)a.table, nullptr, 0, 0, d.scratch, nullptr);
     RTR_LAUNCH_CHECK("contract_kernel (no-alloc)");
     const int64_t count = a.I * a.C;
     reduce_partials_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(d.scratch, (int)gx, count, a.Y,

@@ -65,6 +65,7 @@ struct SketchTCArgs {
     int64_t A, B;
     int I, K, N, MT, rows_cta, S;
     int64_t nchunks, nbc;
+    int64_t aoff;                 // index of the view's first a in the whole tensor (slabs)
     uint64_t seed;
     int mode;
     int vec;                      // 1: 16-byte vector loads are legal
@@ -301,11 +302,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(const SketchTCAr
             int len;
             if (p.B > 1) {
                 const int64_t a = cp.a, b0 = cp.bi * KC;
-                r0 = a * p.B + b0;
+                r0 = (a + p.aoff) * p.B + b0;
                 len = (int)min((int64_t)KC, p.B - b0);
             } else {
                 r0 = ch * KC;
                 len = (int)min((int64_t)KC, p.A - r0);
+                r0 += p.aoff;
             }
             if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
             const uint32_t bt = stage0 + s * stage_bytes + 2 * a_bytes;
@@ -458,6 +460,7 @@ struct SketchTmaArgs {
                                   // FP8: 64 or 32 (whole 32-value scale blocks)
     int fp8;                      // 1: block-scaled float8 values, one MMA (no lo part)
     int64_t nchunks, nbc;
+    int64_t aoff;                 // index of the view's first a in the whole tensor (slabs)
     uint64_t seed;
     int mode;
     const uint16_t* tab;
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
             const int s = r.slot;
             const uint32_t u = r.use;
             const int64_t a = cp.a, b0 = cp.bi * p.kc;
-            const int64_t r0 = a * p.B + b0;
+            const int64_t r0 = (a + p.aoff) * p.B + b0;
             const int len = (int)min((int64_t)p.kc, p.B - b0);
             if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
             const uint32_t bt = sl0 + s * slot_bytes + (uint32_t)MT * TM_TILE;
@@ -777,10 +780,10 @@ int sketch_geometry(int64_t I, int K, int* MT, int* N, int* S, size_t* smem) {
 }  // namespace
 
 int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
-                      double* norm_out, cudaStream_t s) {
+                      double* norm_out, cudaStream_t s, int64_t aoff) {
     const int K = p->K[n];
     SketchTmaArgs a{};
-    a.A = A; a.B = B; a.I = (int)I; a.K = K;
+    a.A = A; a.B = B; a.I = (int)I; a.K = K; a.aoff = aoff;
     a.N = (K <= 32) ? 32 : 64;
     a.fp8 = p->params.prec == RTR_FP8 ? 1 : 0;
     // chunk width: 64, or the largest multiple of 8 up to 64 that divides B
@@ -839,12 +842,12 @@ size_t tc_ws_bytes(const rtr_plan* p) { (void)p; return 0; }
 // (X itself, or an intermediate of the sequential projection): Y = X_(n) Omega_n.
 // norm_out (may be NULL) receives sum x^2 of the tensor.
 int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
-                          double* norm_out, cudaStream_t s) {
+                          double* norm_out, cudaStream_t s, int64_t aoff) {
     const int K = p->K[n];
     const bool aligned16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     const bool fp8 = p->params.prec == RTR_FP8;
     if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
-        return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s);
+        return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s, aoff);
     // the FP8 form exists in the TMA kernel (B > 1) and in the vectorised
     // last-mode path of sketch_tc_kernel only
     if (fp8 && (B > 1 || !aligned16 || I % 4 != 0))
@@ -859,7 +862,7 @@ int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int
     a.X = X; a.A = A; a.B = B; a.I = (int)I; a.K = K; a.N = N; a.MT = MT; a.rows_cta = MT * 128; a.S = S;
     if (B > 1) { a.nbc = rtr_ceil_div(B, KC); a.nchunks = A * a.nbc; }
     else { a.nbc = 1; a.nchunks = rtr_ceil_div(A, KC); }
-    a.seed = p->params.seed; a.mode = n;
+    a.seed = p->params.seed; a.mode = n; a.aoff = aoff;
     a.vec = aligned16 && ((B > 1) ? (B % 4 == 0) : (I % 4 == 0)) ? 1 : 0;
     a.fp8 = fp8 ? 1 : 0;
     a.tab = fp8 ? p->tab_e4m3 : p->tab_bf16;
@@ -887,7 +890,7 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
         if (!p->proj[n]) continue;
         int64_t A, I, B;
         rtr_mode_view(p->N, p->dims, n, &A, &I, &B);
-        const int st = launch_sketch_tc_mode(p, X, A, I, B, n, Y[n], norm_done ? nullptr : p->scal + 0, s);
+        const int st = launch_sketch_tc_mode(p, X, A, I, B, n, Y[n], norm_done ? nullptr : p->scal + 0, s, 0);
         if (st) return st;
         norm_done = true;
     }

@@ -117,7 +117,7 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->chain[0]); cudaFree(p->chain[1]);
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
     cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws); cudaFree(p->ttm_q);
-    cudaFree(p->pow_q); cudaFree(p->pow_t);
+    cudaFree(p->pow_q); cudaFree(p->pow_t); cudaFree(p->acc_y);
     for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
     if (p->als_exec) cudaGraphExecDestroy(p->als_exec);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -326,6 +326,7 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
         RTR_TRY(dalloc(&q, p->ttm_q_bytes));
         p->ttm_q = q;
     }
+    RTR_TRY(dalloc(&p->acc_y, (size_t)maxI * 64));
     if (params->power_iters > 0) {
         // Q of one mode and T = X x_n Q^T for the largest K_n / I_n
         size_t tmax = 1;
@@ -473,7 +474,7 @@ int rtr_project_sequential(rtr_plan* p, const void* X, double* const* Y, double*
         // the first sketch reads X itself and records ||X||^2
         double* norm = step == 0 ? p->scal + 0 : nullptr;
         if (tc) {
-            st = launch_sketch_tc_mode(p, (const float*)cur, A, I, B, n, Y[n], norm, s);
+            st = launch_sketch_tc_mode(p, (const float*)cur, A, I, B, n, Y[n], norm, s, 0);
         } else {
             ContractArgs a{};
             a.X = cur; a.A = A; a.I = I; a.B = B; a.C = p->K[n];
@@ -491,6 +492,152 @@ int rtr_project_sequential(rtr_plan* p, const void* X, double* const* Y, double*
         cd[n] = p->K[n];
         cur = out;
         ++step;
+    }
+    return RTR_OK;
+}
+
+namespace {
+
+// H2D copy of slab `sl` (rows r0 .. r0 + rows - 1 of mode 0) into its stage
+// buffer on the plan's side stream, after the compute that last read that
+// buffer; the caller's stream waits for the copy.
+int stage_in(rtr_plan* p, const void* X_host, int64_t r0, int64_t rows, int64_t row_elems, size_t esz, int64_t sl,
+             void* const* stage, cudaStream_t s) {
+    const int b = sl & 1;
+    cudaEvent_t copied = p->ev[b], done = p->ev[2 + b];
+    if (sl >= 2) RTR_CUDA(cudaStreamWaitEvent(p->side, done, 0));
+    RTR_CUDA(cudaMemcpyAsync(stage[b], static_cast<const char*>(X_host) + (size_t)(r0 * row_elems) * esz,
+                             (size_t)(rows * row_elems) * esz, cudaMemcpyHostToDevice, p->side));
+    RTR_CUDA(cudaEventRecord(copied, p->side));
+    RTR_CUDA(cudaStreamWaitEvent(s, copied, 0));
+    return RTR_OK;
+}
+
+}  // namespace
+
+int rtr_project_host(rtr_plan* p, const void* X_host, int64_t slab_rows, void* const* stage, size_t stage_bytes,
+                     double* const* Y, double* const* Q, void* P, void* stream) {
+    if (!p || !X_host || !stage || !stage[0] || !stage[1] || !Y || !Q || !P)
+        return rtr_set_error(RTR_EINVAL, "NULL argument");
+    const int N = p->N;
+    if (slab_rows < 1 || slab_rows > p->dims[0])
+        return rtr_set_error(RTR_EINVAL, "slab_rows = %lld outside [1, %lld]", (long long)slab_rows,
+                             (long long)p->dims[0]);
+    if (p->order[N - 1] != 0)
+        return rtr_set_error(RTR_EINVAL, "rtr_project_host needs a plan whose chain order ends with mode 0");
+    if (p->params.power_iters != 0) return rtr_set_error(RTR_EINVAL, "rtr_project_host takes no power iterations");
+    for (int n = 0; n < N; ++n) {
+        if (!Q[n]) return rtr_set_error(RTR_EINVAL, "Q[%d] is NULL", n);
+        if (p->proj[n] && !Y[n]) return rtr_set_error(RTR_EINVAL, "Y[%d] is NULL", n);
+    }
+    const int f64 = p->params.prec == RTR_FP64;
+    const bool tc = p->params.prec == RTR_BF16 || p->params.prec == RTR_FP8;
+    const size_t esz = f64 ? 8 : 4;
+    const int64_t row_elems = p->numel / p->dims[0];
+    if (stage_bytes < (size_t)(slab_rows * row_elems) * esz)
+        return rtr_set_error(RTR_EINVAL, "stage buffers of %zu B hold fewer than slab_rows = %lld rows", stage_bytes,
+                             (long long)slab_rows);
+    const int64_t nslabs = rtr_ceil_div(p->dims[0], slab_rows);
+    if (p->params.prec == RTR_FP8 && p->proj[N - 1] && nslabs > 1) {
+        // the last mode's float8 scale blocks run along a: a slab must hold whole blocks
+        int64_t mid = 1;
+        for (int m = 1; m < N - 1; ++m) mid *= p->dims[m];
+        if ((slab_rows * mid) % 32 != 0)
+            return rtr_set_error(RTR_EUNSUPPORTED, "FP8: slab_rows x prod(I_1..I_{N-2}) must be a multiple of 32");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the copies start after the work already queued on the caller's stream
+    RTR_CUDA(cudaEventRecord(p->ev[2], s));
+    RTR_CUDA(cudaStreamWaitEvent(p->side, p->ev[2], 0));
+    int st = RTR_OK;
+    for (int n = 1; n < N; ++n)
+        if (p->proj[n]) RTR_CUDA(cudaMemsetAsync(Y[n], 0, (size_t)p->dims[n] * p->K[n] * sizeof(double), s));
+    RTR_CUDA(cudaMemsetAsync(p->scal + 0, 0, sizeof(double), s));
+
+    // ---- pass 1: sketches, slab by slab
+    for (int64_t sl = 0; sl < nslabs; ++sl) {
+        const int64_t r0 = sl * slab_rows, rows = std::min<int64_t>(slab_rows, p->dims[0] - r0);
+        void* buf = stage[sl & 1];
+        if ((st = stage_in(p, X_host, r0, rows, row_elems, esz, sl, stage, s))) return st;
+        int64_t sd[RTR_MAXN];
+        for (int n = 0; n < N; ++n) sd[n] = p->dims[n];
+        sd[0] = rows;
+        bool norm_done = false;
+        for (int n = 0; n < N; ++n) {
+            if (!p->proj[n]) continue;
+            int64_t A, I, B;
+            rtr_mode_view(N, sd, n, &A, &I, &B);
+            // mode 0: this slab's rows of Y_0 are whole; other modes: this
+            // slab's part of the sum, the test matrix rows counted globally
+            const int64_t aoff = n == 0 ? 0 : r0 * (A / rows);
+            double* ydst = n == 0 ? Y[0] + r0 * p->K[0] : p->acc_y;
+            double* norm = norm_done ? nullptr : p->scal + 2;
+            if (tc) {
+                st = launch_sketch_tc_mode(p, (const float*)buf, A, I, B, n, ydst, norm, s, aoff);
+            } else {
+                ContractArgs a{};
+                a.X = buf; a.A = A; a.I = I; a.B = B; a.C = p->K[n];
+                a.gen = 1; a.seed = p->params.seed; a.mode = n; a.aoff = aoff;
+                a.table = f64 ? (const void*)p->tab64 : (const void*)p->tab32;
+                a.Y = ydst; a.norm_out = norm;
+                st = launch_contract(p, f64, a, s);
+            }
+            if (st) return st;
+            if (n > 0 && (st = launch_add(Y[n], p->acc_y, I * p->K[n], 1, s))) return st;
+            if (!norm_done) {
+                if ((st = launch_add(p->scal + 0, p->scal + 2, 1, 1, s))) return st;
+                norm_done = true;
+            }
+        }
+        if (!norm_done) {
+            if ((st = launch_sumsq(buf, f64, rows * row_elems, p->partial, 1024, p->scal + 2, p->flags, s))) return st;
+            if ((st = launch_add(p->scal + 0, p->scal + 2, 1, 1, s))) return st;
+        }
+        RTR_CUDA(cudaEventRecord(p->ev[2 + (sl & 1)], s));
+    }
+    if ((st = launch_orth(p, Y, Q, s))) return st;
+
+    // ---- pass 2: every product but mode 0's per slab, then the slab's rows of
+    // the mode-0 product added into P
+    if (p->proj[0]) RTR_CUDA(cudaMemsetAsync(P, 0, (size_t)p->pnumel * esz, s));
+    int64_t prest = 1;
+    for (int n = 1; n < N; ++n) prest *= p->K[n];
+    for (int64_t sl = 0; sl < nslabs; ++sl) {
+        const int64_t r0 = sl * slab_rows, rows = std::min<int64_t>(slab_rows, p->dims[0] - r0);
+        const int64_t gsl = nslabs + sl;          // copies so far: pass 1 used nslabs
+        void* buf = stage[gsl & 1];
+        if ((st = stage_in(p, X_host, r0, rows, row_elems, esz, gsl, stage, s))) return st;
+        int64_t cd[RTR_MAXN];
+        for (int n = 0; n < N; ++n) cd[n] = p->dims[n];
+        cd[0] = rows;
+        const void* cur = buf;
+        int step = 0;
+        for (int i = 0; i < N - 1; ++i) {
+            const int n = p->order[i];
+            if (!p->proj[n]) continue;
+            int64_t A, I, B;
+            rtr_mode_view(N, cd, n, &A, &I, &B);
+            void* out = p->chain[step & 1];
+            st = (tc && step == 0) ? launch_ttm_tc(p, (const float*)cur, A, I, B, Q[n], p->K[n], (float*)out, s)
+                                   : launch_ttm(p, f64, cur, A, I, B, Q[n], p->K[n], out, s);
+            if (st) return st;
+            cd[n] = p->K[n];
+            cur = out;
+            ++step;
+        }
+        if (p->proj[0]) {
+            // the stage buffer is free once the first product has read it
+            void* tmp = step == 0 ? p->chain[0] : buf;
+            const size_t cap = step == 0 ? p->chain_bytes[0] : stage_bytes;
+            if ((size_t)p->pnumel * esz > cap) return rtr_set_error(RTR_ENOMEM, "P does not fit the slab buffers");
+            if ((st = launch_ttm(p, f64, cur, 1, rows, prest, Q[0] + r0 * p->K[0], p->K[0], tmp, s))) return st;
+            if ((st = launch_add(P, tmp, p->pnumel, f64, s))) return st;
+        } else {
+            // mode 0 kept whole: this slab's rows of P are the intermediate
+            RTR_CUDA(cudaMemcpyAsync(static_cast<char*>(P) + (size_t)(r0 * prest) * esz, cur,
+                                     (size_t)(rows * prest) * esz, cudaMemcpyDeviceToDevice, s));
+        }
+        RTR_CUDA(cudaEventRecord(p->ev[2 + (gsl & 1)], s));
     }
     return RTR_OK;
 }

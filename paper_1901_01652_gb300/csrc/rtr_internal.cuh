@@ -59,6 +59,7 @@ struct rtr_plan {
     // T = X x_n Q^T in the compute type (max_n |X| K_n / I_n values)
     double* pow_q = nullptr;
     void* pow_t = nullptr;       size_t pow_t_bytes = 0;
+    double* acc_y = nullptr;     // one slab's Y_n (max I_n x 64) before it is added in (rtr_project_host)
 };
 
 // ---- error reporting (rtr_api.cu) -------------------------------------------
@@ -93,8 +94,9 @@ static inline void rtr_mode_view(int N, const int64_t* dims, int n, int64_t* A, 
 struct ContractArgs {
     const void* X; int64_t A; int64_t I; int64_t B;
     int C;
-    // generated operand
-    int gen; uint64_t seed; int mode; const void* table;
+    // generated operand; aoff: index of the view's first a in the whole tensor
+    // (Omega_n row r = (a + aoff) * B + b), 0 unless X is a slab
+    int gen; uint64_t seed; int mode; const void* table; int64_t aoff;
     // stored operand (gen == 0), same element type as X: row r = a*B + b at
     // M[r * ldm + c] (makb = 0), or M laid out (A, C, B), entry (a, c, b) at
     // M[(a * C + c) * B + b] (makb = 1: the output of a mode product)
@@ -116,6 +118,9 @@ int launch_orth_mask(rtr_plan* p, const double* const* Y, double* const* Q, unsi
 // RTR_FLAG_NONFINITE in *flags (when flags is not NULL)
 int launch_sumsq(const void* X, int is_f64, int64_t n, double* part, int nparts, double* out, int* flags,
                  cudaStream_t s);
+
+// y[0 .. n) += x[0 .. n) (float64 or float32)
+int launch_add(void* y, const void* x, int64_t n, int is_f64, cudaStream_t s);
 
 // k_als.cu
 int run_als(rtr_plan* p, const void* P, double* const* Z, int init_given, double* err,
@@ -143,8 +148,9 @@ int batch_als_flags(BatchAls* b, int* flags);
 // k_tc.cu: tensor-core sketch (BF16/FP8 plans) of one mode of a float32
 // tensor viewed as (A, I, B), and of every projected mode of X; the
 // tensor-core product of the last mode (B = 1), other views fall back to launch_ttm
+// aoff: index of the view's first a in the whole tensor (0 unless X is a slab)
 int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
-                          double* norm_out, cudaStream_t s);
+                          double* norm_out, cudaStream_t s, int64_t aoff);
 int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s);
 int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
                   cudaStream_t s);

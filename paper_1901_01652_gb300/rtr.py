@@ -23,7 +23,7 @@ PARAM_NO_GRAPH = 1
 # every entry point of include/rtr.h
 ENTRY_POINTS = (
     "rtr_params_default", "rtr_last_error", "rtr_kernel_launches", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
-    "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_project_sequential", "rtr_als", "rtr_svd", "rtr_backproject",
+    "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_project_sequential", "rtr_project_host", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
     "rtr_sketch_mode_noalloc", "rtr_batch_create", "rtr_batch_destroy", "rtr_batch_run",
     "rtr_batch_graph_kernels", "rtr_batch_flags", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
@@ -69,6 +69,8 @@ def lib():
         "rtr_sketch": (ctypes.c_int, [_VP, _VP, _VPP, _VP]),
         "rtr_project": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
         "rtr_project_sequential": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
+        "rtr_project_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VPP, ctypes.c_size_t, _VPP, _VPP, _VP,
+                                            _VP]),
         "rtr_als": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.c_int, _VP, _VP]),
         "rtr_svd": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VPP, _IP, _VP]),
         "rtr_backproject": (ctypes.c_int, [_VP, _VPP, _VPP, _VPP, _IP, _VP]),
@@ -234,6 +236,27 @@ def rtr_project_sequential(plan, X, Y, Q, P, stream=None):
     _dev(P, plan.x_dtype, "P")
     _check(lib().rtr_project_sequential(plan.handle, _ptr(X), _ptrs(Y, torch.float64, "Y"),
                                         _ptrs(Q, torch.float64, "Q"), _ptr(P), _stream(stream)))
+
+
+def rtr_project_host(plan, X_host, slab_rows, stage, Y, Q, P, stream=None):
+    """Out-of-core steps 3-8: X_host a CPU tensor (pinned for overlapped
+    copies), stage two CUDA tensors of equal size (bytes >= slab_rows rows)."""
+    if not isinstance(X_host, torch.Tensor) or X_host.is_cuda or not X_host.is_contiguous():
+        raise TypeError("X_host must be a contiguous CPU tensor")
+    if X_host.dtype != plan.x_dtype:
+        raise TypeError(f"X_host must be {plan.x_dtype}")
+    if tuple(X_host.shape) != tuple(plan.dims):
+        raise ValueError(f"X_host has shape {tuple(X_host.shape)}, the plan {tuple(plan.dims)}")
+    if len(stage) != 2:
+        raise ValueError("stage must hold two device buffers")
+    for t in stage:
+        _dev(t, None, "stage")
+    nbytes = min(t.numel() * t.element_size() for t in stage)
+    arr = (_VP * 2)(_ptr(stage[0]), _ptr(stage[1]))
+    _dev(P, plan.x_dtype, "P")
+    _check(lib().rtr_project_host(plan.handle, ctypes.c_void_p(X_host.data_ptr()), int(slab_rows), arr, nbytes,
+                                  _ptrs(Y, torch.float64, "Y"), _ptrs(Q, torch.float64, "Q"), _ptr(P),
+                                  _stream(stream)))
 
 
 def rtr_als(plan, P, Z, init_given, err=None, stream=None):
