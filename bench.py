@@ -193,8 +193,8 @@ def parity_vs_oracle(precs, device, seed=1903):
     the benchmark's recipe (TR rank 10 + 30 dB, K = 25, R = 10, 30 sweeps, the
     same start cores on both sides).  Its mode views run the benchmark's
     kernels at the 200^4 launch configurations (mode 1: TMA sketch with two M
-    tiles and 64-wide chunks, as modes 0 and 1 of 200^4; mode 2: 40-wide
-    chunks, as mode 2 of 200^4; mode 3: the last-mode sketch and the first,
+    tiles and 64-wide chunks, as modes 0 and 1 of 200^4; mode 2: 64-wide
+    chunks with a ragged tail, as mode 2 of 200^4; mode 3: the last-mode sketch and the first,
     tensor-core mode product at I = 200, K = 25; mode 0, I = 8 < K, is kept
     whole).  Returns
     {prec: ||Xhat_gpu - Xhat_oracle|| / ||Xhat_oracle||} with the distance

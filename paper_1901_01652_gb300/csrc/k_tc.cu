@@ -442,6 +442,14 @@ __global__ void tc_reduce_kernel(const double* __restrict__ partial, int nparts,
 //   warp 12     TMA producer (one lane)
 //   warp 13     MMA issuer (one lane)
 // (14 warps: at most four per SM sub-partition, so 128 registers a thread)
+//
+// The last mode (B = 1, rows a of I contiguous values) runs the same pipeline
+// without a transpose: a chunk is 64 consecutive a, each 128-row M tile of i
+// arrives as two TMA boxes of 64 a x 64 i (16 KB), converted in place into
+// hi (8 KB) and lo (8 KB) tiles whose 128-byte rows hold 64 consecutive i.
+// Read as the MMA's A operand these tiles are MN-major (M = i contiguous):
+// 8-row groups of a (the K direction) 1024 B apart, the two 64-wide halves
+// of the M tile 16 KB apart.
 constexpr int TM_CONV_WARPS = 8;
 constexpr int TM_RNG_GROUPS = 1;
 constexpr int TM_RNG_WARPS = 4 * TM_RNG_GROUPS;
@@ -459,6 +467,7 @@ struct SketchTmaArgs {
     int kc;                       // chunk width along b: a multiple of 8 dividing B (or 64);
                                   // FP8: 64 or 32 (whole 32-value scale blocks)
     int fp8;                      // 1: block-scaled float8 values, one MMA (no lo part)
+    int lm;                       // 1: the last mode (B = 1, BF16): boxes of 64 a x 64 i, A operand MN-major
     int64_t nchunks, nbc;
     int64_t aoff;                 // index of the view's first a in the whole tensor (slabs)
     uint64_t seed;
@@ -484,6 +493,7 @@ __device__ __forceinline__ bool conv_bar_and(bool v) {
     return r != 0;
 }
 
+template <bool LM>
 __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    const SketchTmaArgs p) {
     extern __shared__ uint8_t smem_raw[];
@@ -566,7 +576,30 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     st_shared_v2(hi + off, h0, h1);
                     st_shared_v2(lo + off, l0, l1);
                 };
-                if (p.kc == 64) {
+                if constexpr (LM) {
+                    // two boxes of 64 a (rows) x 64 i; piece j of this thread: box
+                    // j >> 2, row (ct >> 4) + 16 (j & 3), column group ct & 15
+                    float4 v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int row = (ct >> 4) + 16 * (j & 3);
+                        v[j] = ld_shared_f4(src + (uint32_t)(j >> 2) * 16384u + (uint32_t)row * 256u +
+                                            (uint32_t)(ct & 15) * 16u);
+                        if (want_norm) csum += v[j].x * v[j].x + v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
+                    }
+                    conv_bar();
+                    const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t bx = src + (uint32_t)(j >> 2) * 16384u;
+                        uint32_t h0, l0, h1, l1;
+                        split2(v[j].x, v[j].y, h0, l0);
+                        split2(v[j].z, v[j].w, h1, l1);
+                        const uint32_t off = off0 + 2048u * (uint32_t)(j & 3);
+                        st_shared_v2(bx + off, h0, h1);
+                        st_shared_v2(bx + 8192u + off, l0, l1);
+                    }
+                } else if (p.kc == 64) {
                     // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15
                     float4 v[8];
 #pragma unroll
@@ -642,8 +675,9 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
             const int s = r.slot;
             const uint32_t u = r.use;
             const int64_t a = cp.a, b0 = cp.bi * p.kc;
-            const int64_t r0 = (a + p.aoff) * p.B + b0;
-            const int len = (int)min((int64_t)p.kc, p.B - b0);
+            // last mode: chunk a covers rows 64 a .. 64 a + 63 of the (A, I) view
+            const int64_t r0 = LM ? 64 * a + p.aoff : (a + p.aoff) * p.B + b0;
+            const int len = LM ? (int)min((int64_t)64, p.A - 64 * a) : (int)min((int64_t)p.kc, p.B - b0);
             if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
             const uint32_t bt = sl0 + s * slot_bytes + (uint32_t)MT * TM_TILE;
             for (int item = it0; item < nitems; item += TM_RNG_THREADS) {
@@ -674,14 +708,23 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                 // the full boxes are always counted: out-of-range rows (i >= I) and
                 // columns are zero-filled by the TMA unit without memory traffic
                 mbar_arrive_expect_tx(&full[s], box_bytes * (uint32_t)MT);
-                for (int m = 0; m < MT; ++m)
-                    tma_load_3d(sl0 + s * slot_bytes + m * TM_TILE, &tmap, (int)b0, rbeg + 128 * m, (int)a, &full[s]);
+                if constexpr (LM) {
+                    // boxes {64 i, 64 a}: x = i, y = a
+                    for (int m = 0; m < MT; ++m)
+                        for (int h = 0; h < 2; ++h)
+                            tma_load_2d(sl0 + s * slot_bytes + m * TM_TILE + h * 16384, &tmap, rbeg + 128 * m + 64 * h,
+                                        (int)(64 * a), &full[s]);
+                } else {
+                    for (int m = 0; m < MT; ++m)
+                        tma_load_3d(sl0 + s * slot_bytes + m * TM_TILE, &tmap, (int)b0, rbeg + 128 * m, (int)a,
+                                    &full[s]);
+                }
             }
         }
         __syncwarp();
     } else {
         // ================================================================ MMA issuer
-        const uint32_t idesc = idesc_bf16_f32(128, p.N);
+        const uint32_t idesc = idesc_bf16_f32(128, p.N) | (LM ? IDESC_A_MN_MAJOR : 0u);
         Ring r(S);
         for (int64_t t = 0; t < nloc; ++t, r.step(1)) {
             const int s = r.slot;
@@ -693,8 +736,18 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                 const uint32_t slot = sl0 + s * slot_bytes;
                 const uint32_t bb = slot + (uint32_t)MT * TM_TILE;
                 for (int m = 0; m < MT; ++m) {
-                    const uint32_t ahi = slot + m * TM_TILE, alo = ahi + TM_TILE / 2;
                     const uint32_t d = tmem + (uint32_t)(m * p.N);
+                    if constexpr (LM) {
+                        // MN-major A: K step j = a rows 16 j .. 16 j + 15 (two 8-row groups)
+                        const uint32_t ahi = slot + m * TM_TILE, alo = ahi + 8192u;
+                        for (int j = 0; j < ksteps; ++j) {
+                            const uint64_t bd = sdesc_sw128(bb + 32u * j);
+                            mma_bf16(d, sdesc_sw128_mn(ahi + 2048u * j, 16384u), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
+                            mma_bf16(d, sdesc_sw128_mn(alo + 2048u * j, 16384u), bd, idesc, 1u);
+                        }
+                        continue;
+                    }
+                    const uint32_t ahi = slot + m * TM_TILE, alo = ahi + TM_TILE / 2;
                     for (int j = 0; j < ksteps; ++j) {
                         const uint64_t bd = sdesc_sw128(bb + 32u * j);
                         mma_bf16(d, sdesc_sw128(ahi + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
@@ -784,21 +837,24 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     const int K = p->K[n];
     SketchTmaArgs a{};
     a.A = A; a.B = B; a.I = (int)I; a.K = K; a.aoff = aoff;
+    a.lm = B == 1 ? 1 : 0;
     a.N = (K <= 32) ? 32 : 64;
     a.fp8 = p->params.prec == RTR_FP8 ? 1 : 0;
-    // chunk width: 64, or the largest multiple of 8 up to 64 that divides B
-    // (no ragged tail chunk, e.g. 40 for B = 200).  FP8 chunks hold whole
-    // 32-value scale blocks: 64 or 32, the ragged tail of each b-run
-    // zero-filled by the TMA unit.
+    // chunk width 64: a ragged tail of each b-run is zero-filled by the TMA
+    // unit (for B = 200 the slots then carry 200 of 256 values, against 40
+    // of 64 for 40-wide chunks: 2.37 ms per 200^4 pass against 2.68 ms).
+    // FP8 chunks hold whole 32-value scale blocks: 64, or 32 when B % 64 != 0.
     a.kc = 64;
-    if (a.fp8) {
-        if (B % 64 != 0) a.kc = 32;
-    } else if (B % 64 != 0) {
-        for (int w = 56; w >= 8; w -= 8)
-            if (B % w == 0) { a.kc = w; break; }
+    if (a.fp8 && B % 64 != 0) a.kc = 32;
+    if (a.lm) {
+        // the last mode: chunks of 64 consecutive a, boxes of 64 a x 64 i
+        a.kc = 64;
+        a.nbc = 1;
+        a.nchunks = rtr_ceil_div(A, 64);
+    } else {
+        a.nbc = rtr_ceil_div(B, a.kc);
+        a.nchunks = A * a.nbc;
     }
-    a.nbc = rtr_ceil_div(B, a.kc);
-    a.nchunks = A * a.nbc;
     a.seed = p->params.seed; a.mode = n;
     a.tab = a.fp8 ? p->tab_e4m3 : p->tab_bf16; a.flags = p->flags;
     // a CTA covers up to 256 rows: MT = 2 tiles of 128 when the view has more than 128
@@ -816,17 +872,32 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     a.partial = p->partial;
     a.normp = norm_out ? p->normx_part : nullptr;
     CUtensorMap tmap;
-    const cuuint64_t gdim[3] = {(cuuint64_t)B, (cuuint64_t)I, (cuuint64_t)A};
-    const cuuint64_t gstride[2] = {(cuuint64_t)B * 4, (cuuint64_t)I * B * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)a.kc, 128, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), gdim,
-                                             gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult cr;
+    if (a.lm) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)I, (cuuint64_t)A};
+        const cuuint64_t gstride[1] = {(cuuint64_t)I * 4};
+        const cuuint32_t box[2] = {64, 64};
+        const cuuint32_t estr[2] = {1, 1};
+        cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), gdim, gstride, box,
+                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t gdim[3] = {(cuuint64_t)B, (cuuint64_t)I, (cuuint64_t)A};
+        const cuuint64_t gstride[2] = {(cuuint64_t)B * 4, (cuuint64_t)I * B * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)a.kc, 128, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), gdim, gstride, box,
+                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-    RTR_CUDA(cudaFuncSetAttribute(sketch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    sketch_tma_kernel<<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+    if (a.lm) {
+        RTR_CUDA(cudaFuncSetAttribute(sketch_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sketch_tma_kernel<true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+    } else {
+        RTR_CUDA(cudaFuncSetAttribute(sketch_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sketch_tma_kernel<false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+    }
     RTR_LAUNCH_CHECK("sketch_tma_kernel");
     const int64_t count = I * K;
     tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(p->partial, (int)gx, count, Y,
@@ -847,6 +918,10 @@ int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int
     const bool aligned16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     const bool fp8 = p->params.prec == RTR_FP8;
     if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
+        return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s, aoff);
+    // the last mode on the same pipeline (BF16; the FP8 form's scale blocks run
+    // along a, across the converter threads, so it keeps sketch_tc_kernel)
+    if (B == 1 && !fp8 && I % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
         return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s, aoff);
     // the FP8 form exists in the TMA kernel (B > 1) and in the vectorised
     // last-mode path of sketch_tc_kernel only
@@ -903,51 +978,65 @@ int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t
 //     T[a, k] = sum_i X[a, i] Q[i, k]
 // D += Xhi Qhi + Xlo Qhi + Xhi Qlo on tcgen05 (BF16 inputs, FP32 accumulation);
 // Q (float64) is split once into resident bf16 hi/lo tiles.  Work unit = one
-// 128-row tile of X and one 64-wide chunk of i.  Warps: 8 converters (loads
-// prefetched one unit ahead), 1 MMA issuer, 4 epilogue warps draining a
-// double-buffered TMEM accumulator into T.
+// 128-row tile of X and one 64-wide chunk of i, loaded by TMA as a box of
+// 128 rows x 64 float32 into a ring slot and converted there in place into
+// its hi (first 16 KB) and lo (second 16 KB) operand tiles, as in the sketch.
+// Warps: 8 converters, 1 MMA issuer, 4 epilogue warps draining a
+// double-buffered TMEM accumulator into T, 1 TMA producer.
 namespace {
 
 constexpr int TT_CONV_WARPS = 8;
 constexpr int TT_MMA_WARP = TT_CONV_WARPS;
-constexpr int TT_NTHREADS = (TT_CONV_WARPS + 1 + 4) * 32;    // converters, MMA issuer, 4 epilogue warps
+constexpr int TT_TMA_WARP = TT_CONV_WARPS + 1 + 4;
+constexpr int TT_NTHREADS = (TT_TMA_WARP + 1) * 32;       // converters, MMA issuer, 4 epilogue warps, TMA
 constexpr int TT_CONV_THREADS = TT_CONV_WARPS * 32;
 constexpr int TT_PIECES = 128 * 16 / TT_CONV_THREADS;    // float4 pieces per converter thread per unit
 
 struct TtmTCArgs {
-    const float* X;
     const double* Q;
     float* out;
     int64_t A;
-    int I, K, N, NKC, S, vec;
+    int I, K, N, NKC, S;
     int64_t ntiles;
     int* flags;
 };
 
-__global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs p) {
+// named barrier 2 among the product's converter threads
+__device__ __forceinline__ void tt_conv_bar() {
+    asm volatile("bar.sync 2, %0;" ::"n"(TT_CONV_THREADS) : "memory");
+}
+__device__ __forceinline__ bool tt_conv_bar_and(bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred pv, pr;\n\tsetp.ne.u32 pv, %1, 0;\n\tbar.red.and.pred pr, 2, %2, pv;\n\t"
+                 "selp.u32 %0, 1, 0, pr;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v), "n"(TT_CONV_THREADS) : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                               const TtmTCArgs p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t* sm = smem_raw + pad;
     const uint32_t btile = (uint32_t)p.N * 128u;
     const uint32_t b_bytes = 2u * p.NKC * btile;               // Q hi tiles, then Q lo tiles
-    const uint32_t a_stage = 2u * MTILE_BYTES;                 // X hi, X lo
+    const uint32_t a_stage = 2u * MTILE_BYTES;                 // one box of 128 x 64 float32 = X hi + X lo
     const int S = p.S;
     const uint32_t bbase = smem_u32(sm);
     const uint32_t abase = bbase + b_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + b_bytes + S * a_stage);
-    uint64_t* fullA = bars;
-    uint64_t* empty = bars + S;
-    uint64_t* accf = bars + 2 * S;      // [2]
-    uint64_t* acce = bars + 2 * S + 2;  // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
+    uint64_t* full = bars;              // TMA landed
+    uint64_t* conv = bars + S;          // operand tiles written (8 converter warps)
+    uint64_t* empty = bars + 2 * S;     // MMAs of the slot done
+    uint64_t* accf = bars + 3 * S;      // [2]
+    uint64_t* acce = bars + 3 * S + 2;  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t ncols = 2u * p.N;
 
-    // ---- set-up: zero A stages, build Q hi/lo tiles, barriers, TMEM
-    for (uint32_t off = tid * 16u; off < (uint32_t)S * a_stage; off += TT_NTHREADS * 16u)
-        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(abase + off), "r"(0) : "memory");
+    // ---- set-up: Q hi/lo tiles, barriers, TMEM
     for (int e = tid; e < p.NKC * p.N * 32; e += TT_NTHREADS) {
         const int c = e / (p.N * 32), rem = e % (p.N * 32);
         const int k = rem / 32, ip = rem % 32;          // bf16 pair (2 ip, 2 ip + 1) of chunk c, row k
@@ -962,7 +1051,8 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&fullA[s], TT_CONV_THREADS);
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], TT_CONV_WARPS);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -984,73 +1074,28 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
     if (warp < TT_CONV_WARPS) {
         // ================================================================ converters
         const int ct = tid;
-        // units are loaded in order u = 0, 1, ...: (tile j, i-chunk c) advanced in step
-        int64_t lj = 0;
-        int lc = 0;
-        auto load = [&](float4 (&v)[TT_PIECES]) {
-            const int64_t j = lj;
-            const int c = lc;
-            if (++lc == p.NKC) { lc = 0; ++lj; }
-            const int64_t a0 = (blockIdx.x + j * gridDim.x) * 128;
-            const int rows = (int)min((int64_t)128, p.A - a0);
+        const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+        Ring rg(S);
+        for (int64_t u = 0; u < nunits; ++u, rg.step(1)) {
+            const int s = rg.slot;
+            if (!tt_conv_bar_and(mbar_wait(&full[s], rg.use & 1, abort, p.flags))) break;
+            const uint32_t src = abase + s * a_stage;
+            float4 v[TT_PIECES];
+#pragma unroll
+            for (int q = 0; q < TT_PIECES; ++q)
+                v[q] = ld_shared_f4(src + (uint32_t)((ct >> 4) + 16 * q) * 256u + (uint32_t)(ct & 15) * 16u);
+            tt_conv_bar();                            // every piece of the box is in registers
 #pragma unroll
             for (int q = 0; q < TT_PIECES; ++q) {
-                const int pc = ct + TT_CONV_THREADS * q;
-                const int row = pc >> 4, c4 = pc & 15;
-                const int i = c * 64 + 4 * c4;
-                v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (row < rows && i < p.I) {
-                    const float* src = p.X + (a0 + row) * (int64_t)p.I + i;
-                    if (p.vec) v[q] = __ldg(reinterpret_cast<const float4*>(src));
-                    else {
-                        v[q].x = src[0];
-                        if (i + 1 < p.I) v[q].y = src[1];
-                        if (i + 2 < p.I) v[q].z = src[2];
-                        if (i + 3 < p.I) v[q].w = src[3];
-                    }
-                }
-            }
-        };
-        auto store = [&](int s, const float4 (&v)[TT_PIECES]) {
-            const uint32_t hi = abase + s * a_stage, lo = hi + MTILE_BYTES;
-#pragma unroll
-            for (int q = 0; q < TT_PIECES; ++q) {
-                const int pc = ct + TT_CONV_THREADS * q;
-                const int row = pc >> 4, c4 = pc & 15;
                 uint32_t h0, l0, h1, l1;
                 split2(v[q].x, v[q].y, h0, l0);
                 split2(v[q].z, v[q].w, h1, l1);
-                const uint32_t off = sw128_off(row, 4 * c4);
-                st_shared_v2(hi + off, h0, h1);
-                st_shared_v2(lo + off, l0, l1);
+                st_shared_v2(src + off0 + 2048u * q, h0, h1);
+                st_shared_v2(src + MTILE_BYTES + off0 + 2048u * q, l0, l1);
             }
-        };
-        float4 va[TT_PIECES], vb[TT_PIECES];
-        Ring rg(S);                                   // slot / use of the unit being stored
-        if (nunits > 0) load(va);
-        for (int64_t u = 0; u < nunits; u += 2) {
-            // unit u in va (loaded earlier); prefetch u + 1 into vb
-            if (u + 1 < nunits) load(vb);
-            {
-                const int s = rg.slot;
-                const uint32_t ph = rg.use;
-                if (u >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
-                store(s, va);
-                fence_proxy_async();
-                mbar_arrive(&fullA[s]);
-                rg.step(1);
-            }
-            if (u + 1 >= nunits) break;
-            if (u + 2 < nunits) load(va);
-            {
-                const int s = rg.slot;
-                const uint32_t ph = rg.use;
-                if (u + 1 >= S && !mbar_wait(&empty[s], (ph - 1) & 1, abort, p.flags)) break;
-                store(s, vb);
-                fence_proxy_async();
-                mbar_arrive(&fullA[s]);
-                rg.step(1);
-            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[s]);
         }
     } else if (warp == TT_MMA_WARP) {
         // ================================================================ MMA issuer
@@ -1064,7 +1109,7 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
             const uint32_t d = tmem + (uint32_t)(buf * p.N);
             for (int c = 0; c < p.NKC; ++c, rg.step(1)) {
                 const int s = rg.slot;
-                if (!mbar_wait(&fullA[s], rg.use & 1, abort, p.flags)) { ok = false; break; }
+                if (!mbar_wait(&conv[s], rg.use & 1, abort, p.flags)) { ok = false; break; }
                 tc_fence_after();
                 if (lane == 0) {
                     const uint32_t ahi = abase + s * a_stage, alo = ahi + MTILE_BYTES;
@@ -1084,7 +1129,7 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
             if (ok && lane == 0) mma_commit(&accf[buf]);
             __syncwarp();
         }
-    } else {
+    } else if (warp < TT_TMA_WARP) {
         // ================================================================ epilogue
         const int g = warp & 3;                       // TMEM lane group of this warp
         for (int64_t j = 0; j < nloc; ++j) {
@@ -1106,6 +1151,23 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
             tc_fence_before();
             mbar_arrive(&acce[buf]);
         }
+    } else {
+        // ================================================================ TMA producer
+        if (lane == 0) {
+            Ring rg(S);
+            int64_t j = 0;
+            int c = 0;
+            for (int64_t u = 0; u < nunits; ++u, rg.step(1)) {
+                const int s = rg.slot;
+                if (u >= S && !mbar_wait(&empty[s], (rg.use - 1) & 1, abort, p.flags)) break;
+                const int64_t a0 = (blockIdx.x + j * gridDim.x) * 128;
+                // rows a >= A and columns i >= I are zero-filled without memory traffic
+                mbar_arrive_expect_tx(&full[s], (uint32_t)a_stage);
+                tma_load_2d(abase + s * a_stage, &tmap, c * 64, (int)a0, &full[s]);
+                if (++c == p.NKC) { c = 0; ++j; }
+            }
+        }
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -1117,15 +1179,16 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const TtmTCArgs 
 
 int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
                   cudaStream_t s) {
-    if (B != 1 || I > 256 || K > 64) {
+    const bool tma_ok = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && I % 4 == 0 && A < ((int64_t)1 << 31) &&
+                        tensor_map_encoder();
+    if (B != 1 || I > 256 || K > 64 || !tma_ok) {
         // other mode products of BF16 plans run on the SIMT FP32 kernel
         return launch_ttm(p, 0, X, A, I, B, Q, K, out, s);
     }
     TtmTCArgs a{};
-    a.X = X; a.Q = Q; a.out = out; a.A = A; a.I = (int)I; a.K = K;
+    a.Q = Q; a.out = out; a.A = A; a.I = (int)I; a.K = K;
     a.N = (K <= 32) ? 32 : 64;
     a.NKC = (int)rtr_ceil_div(I, 64);
-    a.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && I % 4 == 0) ? 1 : 0;
     a.ntiles = rtr_ceil_div(A, 128);
     a.flags = p->flags;
     const size_t bq = 2 * (size_t)a.NKC * a.N * 128;
@@ -1135,9 +1198,19 @@ int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, 
     if (S < 2) return launch_ttm(p, 0, X, A, I, B, Q, K, out, s);
     a.S = S;
     const size_t smem = fixed + bq + (size_t)S * 2 * MTILE_BYTES;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)I, (cuuint64_t)A};
+    const cuuint64_t gstride[1] = {(cuuint64_t)I * 4};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), gdim,
+                                             gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(a.ntiles, p->num_sms));
     RTR_CUDA(cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ttm_tc_kernel<<<(unsigned)gx, TT_NTHREADS, smem, s>>>(a);
+    ttm_tc_kernel<<<(unsigned)gx, TT_NTHREADS, smem, s>>>(tmap, a);
     RTR_LAUNCH_CHECK("ttm_tc_kernel");
     return RTR_OK;
 }

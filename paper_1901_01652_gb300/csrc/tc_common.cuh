@@ -128,6 +128,24 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor: MN-major operand (the M or N index
+// contiguous), 128-byte swizzle: 128-byte rows hold 64 consecutive M (N)
+// values of one K index; 8-row groups along K are 1024 bytes apart (stride
+// byte offset) and the 64-wide blocks along M (N) are `mn_stride` bytes apart
+// (leading byte offset).
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t mn_stride) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)((mn_stride >> 4) & 0x3FFF) << 16; // leading byte offset: next 64 M (N) values
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: next 8 K rows
+    d |= (uint64_t)1 << 46;                            // descriptor version (sm_100)
+    d |= (uint64_t)2 << 61;                            // layout: SWIZZLE_128B
+    return d;
+}
+
+// instruction-descriptor bit: the A operand is MN-major
+constexpr uint32_t IDESC_A_MN_MAJOR = 1u << 15;
+
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                     // D format F32

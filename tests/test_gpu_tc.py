@@ -36,6 +36,33 @@ TC_CASES = [
 ]
 
 
+LAST_MODE_CASES = [
+    ((300, 200), (7, 25)),                    # I = 200: two M tiles, the second ragged; A = 300 (ragged chunk)
+    ((2, 3, 5, 64), (1, 2, 4, 20)),           # I = 64: one M tile, half of it past I; A = 30 < 64
+    ((97, 300), (5, 33)),                     # I = 300: two row blocks (256 + 44), N = 64
+    ((130, 128), (9, 64)),                    # I = 128 exactly one M tile, K = 64
+]
+
+
+@pytest.mark.parametrize("dims,K", LAST_MODE_CASES)
+def test_bf16_last_mode_tma_sketch_vs_oracle(dims, K):
+    """The last mode through the TMA sketch with an MN-major operand: boxes of
+    64 rows x 64 columns, zero-filled past I and past A."""
+    dims = tuple(dims)
+    full = dims if len(dims) >= 3 else (1,) + dims
+    Kf = K if len(K) >= 3 else (1,) + tuple(K)
+    X32 = np.random.default_rng(25).standard_normal(full).astype(np.float32)
+    plan = rtr.rtr_plan_create(full, Kf, (2,) * len(full), rtr.make_params("bf16", 79))
+    Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") if pr else None
+         for d, k, pr in zip(plan.dims, plan.K, plan.projected)]
+    rtr.rtr_sketch(plan, torch.from_numpy(X32).cuda(), Y)
+    torch.cuda.synchronize()
+    assert rtr.rtr_plan_flags(plan) == 0
+    ref = orc.sketch(X32.astype(np.float64), Kf, 79, "bf16")
+    n = len(full) - 1
+    assert rel(Y[n].cpu().numpy(), ref[n]) < 2e-5
+
+
 @pytest.mark.parametrize("dims,K", TC_CASES)
 def test_bf16_sketch_vs_oracle(dims, K):
     X32 = np.random.default_rng(21).standard_normal(dims).astype(np.float32)
@@ -106,9 +133,10 @@ def test_bf16_sketch_and_chain_at_the_200x4_kernel_configurations():
     a 200 x 8 x 200 x 200 tensor (K = 25; mode 1, I = 8 < K, is kept whole):
     mode 0 (view 1 x 200 x 320000) runs the TMA sketch with two M tiles and
     full 64-wide chunks, as modes 0 and 1 of 200^4 do; mode 2 (1600 x 200 x
-    200) runs it with 40-wide chunks, as mode 2 of 200^4 does; mode 3 runs the
-    last-mode sketch at I = 200; the chain starts with the last mode's product
-    on the tensor cores at I = 200, K = 25."""
+    200) runs it with 64-wide chunks whose last one per b-run is ragged (8 of
+    64), as mode 2 of 200^4 does; mode 3 runs the last-mode TMA sketch (MN-major
+    operand) at I = 200; the chain starts with the last mode's product on the
+    tensor cores at I = 200, K = 25."""
     dims, K = (200, 8, 200, 200), (25, 25, 25, 25)
     X32 = np.random.default_rng(24).standard_normal(dims).astype(np.float32)
     X = X32.astype(np.float64)
