@@ -542,7 +542,11 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     const uint32_t tmem = *tmem_slot;
     const int rbeg = blockIdx.y * 256;
     const int rows_valid = min(128 * MT, p.I - rbeg);
-    const int64_t nloc = (blockIdx.x < p.nchunks) ? (p.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // each CTA takes a contiguous range of chunks (its successive boxes are
+    // adjacent in b: 2% faster at 200^4 than a grid-stride assignment)
+    const int64_t per_cta = p.nchunks / gridDim.x, rem_cta = p.nchunks % gridDim.x;
+    const int64_t c0 = blockIdx.x * per_cta + min((int64_t)blockIdx.x, rem_cta);
+    const int64_t nloc = per_cta + ((int64_t)blockIdx.x < rem_cta ? 1 : 0);
     const int ksteps = (p.kc + 15) >> 4;          // operand columns kc .. 16 ksteps - 1 are written as zeros
     double nsum = 0.0;
 
@@ -589,15 +593,65 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     }
                     conv_bar();
                     const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+                    if (p.fp8) {
+                        // float8 scale blocks run along a: rows 0-31 and 32-63 of each
+                        // column.  This thread's rows of block b are pieces 2b, 2b + 1;
+                        // the partner lane (lane ^ 16) holds the next row; the other
+                        // rows sit in the other 7 converter warps, met through the
+                        // box's lo half (unused by the FP8 form) after the barrier above
+                        float4 mx[2][2];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const uint32_t bx = src + (uint32_t)(j >> 2) * 16384u;
-                        uint32_t h0, l0, h1, l1;
-                        split2(v[j].x, v[j].y, h0, l0);
-                        split2(v[j].z, v[j].w, h1, l1);
-                        const uint32_t off = off0 + 2048u * (uint32_t)(j & 3);
-                        st_shared_v2(bx + off, h0, h1);
-                        st_shared_v2(bx + 8192u + off, l0, l1);
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                const float4 a0 = v[4 * h + 2 * b], a1 = v[4 * h + 2 * b + 1];
+                                float4 m = make_float4(fmaxf(fabsf(a0.x), fabsf(a1.x)), fmaxf(fabsf(a0.y), fabsf(a1.y)),
+                                                       fmaxf(fabsf(a0.z), fabsf(a1.z)), fmaxf(fabsf(a0.w), fabsf(a1.w)));
+                                m.x = fmaxf(m.x, __shfl_xor_sync(0xffffffffu, m.x, 16));
+                                m.y = fmaxf(m.y, __shfl_xor_sync(0xffffffffu, m.y, 16));
+                                m.z = fmaxf(m.z, __shfl_xor_sync(0xffffffffu, m.z, 16));
+                                m.w = fmaxf(m.w, __shfl_xor_sync(0xffffffffu, m.w, 16));
+                                mx[h][b] = m;
+                            }
+                        // exchange slots: box h's lo half, [block][warp][64 columns] floats
+                        if (lane < 16)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                                for (int b = 0; b < 2; ++b)
+                                    st_shared_v4f(src + (uint32_t)h * 16384u + 8192u +
+                                                      (uint32_t)((b * TM_CONV_WARPS + warp) * 64 + 4 * (ct & 15)) * 4u,
+                                                  mx[h][b]);
+                        conv_bar();
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+                                for (int w = 0; w < TM_CONV_WARPS; ++w) {
+                                    const float4 o = ld_shared_f4(src + (uint32_t)h * 16384u + 8192u +
+                                                                  (uint32_t)((b * TM_CONV_WARPS + w) * 64 + 4 * (ct & 15)) * 4u);
+                                    m = make_float4(fmaxf(m.x, o.x), fmaxf(m.y, o.y), fmaxf(m.z, o.z), fmaxf(m.w, o.w));
+                                }
+                                const MxScale s0 = mx_scale(m.x), s1 = mx_scale(m.y), s2 = mx_scale(m.z), s3 = mx_scale(m.w);
+#pragma unroll
+                                for (int jj = 0; jj < 2; ++jj) {
+                                    const int j = 4 * h + 2 * b + jj;
+                                    st_shared_v2(src + (uint32_t)h * 16384u + off0 + 2048u * (uint32_t)(j & 3),
+                                                 mx_pair2(v[j].x, v[j].y, s0, s1), mx_pair2(v[j].z, v[j].w, s2, s3));
+                                }
+                            }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint32_t bx = src + (uint32_t)(j >> 2) * 16384u;
+                            uint32_t h0, l0, h1, l1;
+                            split2(v[j].x, v[j].y, h0, l0);
+                            split2(v[j].z, v[j].w, h1, l1);
+                            const uint32_t off = off0 + 2048u * (uint32_t)(j & 3);
+                            st_shared_v2(bx + off, h0, h1);
+                            st_shared_v2(bx + 8192u + off, l0, l1);
+                        }
                     }
                 } else if (p.kc == 64) {
                     // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15
@@ -670,7 +724,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
         const int it0 = rt, it1 = rt + TM_RNG_THREADS;
         const int rr0 = it0 % p.kc, cb0 = it0 / p.kc, rr1 = it1 % p.kc, cb1 = it1 / p.kc;
         Ring r(S, grp);
-        ChunkPos cp(blockIdx.x + (int64_t)grp * gridDim.x, (int64_t)TM_RNG_GROUPS * gridDim.x, p.nbc);
+        ChunkPos cp(c0 + grp, (int64_t)TM_RNG_GROUPS, p.nbc);
         for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS, r.step(TM_RNG_GROUPS), cp.step()) {
             const int s = r.slot;
             const uint32_t u = r.use;
@@ -698,7 +752,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
         // ================================================================ TMA producer
         if (lane == 0) {
             Ring r(S);
-            ChunkPos cp(blockIdx.x, gridDim.x, p.nbc);
+            ChunkPos cp(c0, 1, p.nbc);
             const uint32_t box_bytes = (uint32_t)(128 * 4 * p.kc);
             for (int64_t t = 0; t < nloc; ++t, r.step(1), cp.step()) {
                 const int s = r.slot;
@@ -743,7 +797,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                         for (int j = 0; j < ksteps; ++j) {
                             const uint64_t bd = sdesc_sw128(bb + 32u * j);
                             mma_bf16(d, sdesc_sw128_mn(ahi + 2048u * j, 16384u), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                            mma_bf16(d, sdesc_sw128_mn(alo + 2048u * j, 16384u), bd, idesc, 1u);
+                            if (!p.fp8) mma_bf16(d, sdesc_sw128_mn(alo + 2048u * j, 16384u), bd, idesc, 1u);
                         }
                         continue;
                     }
@@ -919,9 +973,8 @@ int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int
     const bool fp8 = p->params.prec == RTR_FP8;
     if (B > 1 && B % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
         return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s, aoff);
-    // the last mode on the same pipeline (BF16; the FP8 form's scale blocks run
-    // along a, across the converter threads, so it keeps sketch_tc_kernel)
-    if (B == 1 && !fp8 && I % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
+    // the last mode on the same pipeline (BF16 and FP8)
+    if (B == 1 && I % 4 == 0 && aligned16 && A < ((int64_t)1 << 31) && tensor_map_encoder())
         return launch_sketch_tma(p, X, A, I, B, n, Y, norm_out, s, aoff);
     // the FP8 form exists in the TMA kernel (B > 1) and in the vectorised
     // last-mode path of sketch_tc_kernel only

@@ -223,6 +223,21 @@ __device__ __forceinline__ uint32_t mx_pair(float x0, float x1, const MxScale& m
     return *reinterpret_cast<uint32_t*>(&b);
 }
 
+// as mx_pair with its own scale for each of the two values
+__device__ __forceinline__ uint32_t mx_pair2(float x0, float x1, const MxScale& m0, const MxScale& m1) {
+    const __nv_fp8x2_storage_t q =
+        __nv_cvt_float2_to_fp8x2(make_float2(x0 * m0.inv, x1 * m1.inv), __NV_SATFINITE, __NV_E4M3);
+    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
+    const float2 f = __half22float2(__half2(hr));
+    __nv_bfloat162 b = __floats2bfloat162_rn(f.x * m0.s, f.y * m1.s);
+    return *reinterpret_cast<uint32_t*>(&b);
+}
+
+__device__ __forceinline__ void st_shared_v4f(uint32_t addr, const float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 // maximum over aligned groups of `width` lanes (width a power of two <= 32)
 __device__ __forceinline__ float group_max(float v, int width) {
     for (int o = 1; o < width; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));

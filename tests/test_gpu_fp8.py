@@ -34,6 +34,8 @@ FP8_CASES = [
     ((5, 300, 36), (3, 40, 7)),              # three row groups, B = 36: one full and one ragged chunk
     ((33, 70, 200), (20, 64, 60)),           # K = 64 and K = 60; B = 200: ragged last block of 8
     ((64, 48, 32), (12, 12, 8)),             # the hyperspectral-shaped test tensor
+    ((37, 5, 24), (9, 4, 6)),                # last mode: A = 185 rows, the last scale block of 25
+    ((3, 7, 300), (2, 5, 20)),               # last mode I = 300: two row blocks of the TMA sketch
 ]
 
 
