@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-parity", action="store_true", help="skip the reduced-tensor parity check vs the oracle")
+    ap.add_argument("--inflight", type=int, default=2,
+                    help="tensors in flight: consecutive steps on this many streams, each with its own plan, so that "
+                         "one tensor's TR-ALS overlaps the next one's sketch (1 = one step after the other)")
     ap.add_argument("--workload", default="c2", choices=["c2", "batch256", "c1", "c3"],
                     help="c2 = the 200^4 tensor (default); batch256 = 256 uneven image-like tensors; "
                          "c1 = FP64 60^4 TR-ALS; c3 = hyperspectral-shaped 1024x1024x256 TR-SVD")
@@ -246,6 +249,39 @@ def pipeline_bytes(dims, K, order, elem=4):
     return 2 * numel * elem + inter, (nproj + 1) * numel * elem + inter
 
 
+def time_steps_inflight(pipes, streams, X, steps, warmup, dist_max):
+    """K steps with step i on streams[i % len(streams)] (its own plan), so that
+    up to len(streams) tensors are in flight; every step runs the whole path.
+    Returns (max-over-ranks ms for the K steps, kernel launches)."""
+    import torch
+    from paper_1901_01652_gb300 import rtr
+    main = torch.cuda.current_stream()
+
+    def run(n):
+        for s in streams:
+            s.wait_stream(main)
+        for i in range(n):
+            k = i % len(pipes)
+            with torch.cuda.stream(streams[k]):
+                pipes[k].step(X, streams[k])
+        for s in streams:
+            main.wait_stream(s)
+
+    run(warmup)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist_barrier()
+    torch.cuda.synchronize()
+    l0 = rtr.rtr_kernel_launches()
+    t0.record(main)
+    run(steps)
+    t1.record(main)
+    torch.cuda.synchronize()
+    l1 = rtr.rtr_kernel_launches()
+    dist_barrier()
+    return dist_max(t0.elapsed_time(t1)), l1 - l0
+
+
 def time_steps(pipe, X, steps, warmup, stream, dist_max):
     import torch
     from paper_1901_01652_gb300 import rtr
@@ -325,9 +361,18 @@ def run_ours(args):
     xbytes = X.numel() * 4
     stream = torch.cuda.current_stream(device)
 
-    pipe = Pipeline(dims, K, R, sweeps, args.prec, 1903, device)
+    inflight = max(1, args.inflight)
+    pipes = [Pipeline(dims, K, R, sweeps, args.prec, 1903, device) for _ in range(inflight)]
+    pipe = pipes[0]
     with ClockSampler(local) as clk:
-        ms, phases, launches = time_steps(pipe, X, args.steps, args.warmup, stream, dist_max)
+        if inflight > 1:
+            streams = [torch.cuda.Stream(device) for _ in range(inflight)]
+            ms, launches = time_steps_inflight(pipes, streams, X, args.steps, args.warmup, dist_max)
+        else:
+            ms, phases, launches = time_steps(pipe, X, args.steps, args.warmup, stream, dist_max)
+    if inflight > 1:
+        # phase times and the sketch's roofline from steps run one after the other
+        _, phases, _ = time_steps(pipe, X, max(2, args.steps // 2), 1, stream, dist_max)
     sk_ms = phases[0]
     clocks = clk.summary()
     ms_step = ms / args.steps
@@ -342,7 +387,8 @@ def run_ours(args):
         "dtype": {"bf16": "bf16", "fp32": "f32", "fp8": "fp8-e4m3 sketch, bf16 chain"}[args.prec], "data": "synthetic",
         "config": {"workload": WORKLOAD if S == 200 else f"rTR-ALS order-4 {S}^4 fp32 (reduced)",
                    "dims": list(dims), "K": list(K), "R": list(R), "sweeps": sweeps, "snr_db": snr,
-                   "prec": args.prec, "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+                   "prec": args.prec, "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
+                   "inflight": inflight},
         "rse": rse_mixed,
         "phases_ms": {"sketch": round(phases[0], 4), "project": round(phases[1], 4), "als": round(phases[2], 4),
                       "backproject_rse": round(phases[3], 4)},
@@ -368,10 +414,15 @@ def run_ours(args):
                        "pipeline_frac_per_mode": round(per_mode / (ph_ms * 1e-3) / 1e9 / peak, 4)}
     # plain FP32 arm on the same tensor
     if not args.no_plain and args.prec != "fp32":
-        plain = Pipeline(dims, K, R, sweeps, "fp32", 1903, device)
-        pms, pph, _ = time_steps(plain, X, max(1, args.steps // 2), 1, stream, dist_max)
+        plains = [Pipeline(dims, K, R, sweeps, "fp32", 1903, device) for _ in range(inflight)]
+        plain = plains[0]
+        psteps = max(2, args.steps // 2)
+        if inflight > 1:
+            pms, _ = time_steps_inflight(plains, streams, X, psteps, inflight, dist_max)
+            _, pph, _ = time_steps(plain, X, 1, 0, stream, dist_max)
+        else:
+            pms, pph, _ = time_steps(plain, X, psteps, 1, stream, dist_max)
         psk = pph[0]
-        psteps = max(1, args.steps // 2)
         torch.cuda.synchronize()
         rse_plain = float(plain.eng.rse.cpu()[0])
         Xm = pipe.eng.reconstruct("fp32")
@@ -385,28 +436,32 @@ def run_ours(args):
                              "phases_ms": {"sketch": round(pph[0], 4), "project": round(pph[1], 4),
                                            "als": round(pph[2], 4), "backproject_rse": round(pph[3], 4)}}
         out["mixed_vs_plain_rel_diff"] = diff
-        del plain
-    # end to end through the public API with host buffers
+        del plain, plains
+    # end to end through the public API with host buffers: a stream of host
+    # tensors, `inflight` of them in flight (copies overlap the other's compute)
     if not args.no_e2e:
-        from paper_1901_01652_gb300.api import decompose
+        from paper_1901_01652_gb300.api import decompose_stream
         Xh = X.cpu().pin_memory()
-        ek = max(1, min(args.steps, 3))
-        decompose(Xh, K, R, "als", args.prec, 1903, sweeps, init=pipe.init, engine=pipe.eng)
+        del X
+        torch.cuda.empty_cache()
+        ek = max(2 * inflight, min(args.steps, 6))
+        engs = [p.eng for p in pipes]
+        decompose_stream([Xh] * inflight, K, R, "als", args.prec, 1903, sweeps, init=pipe.init, engines=engs)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        for _ in range(ek):
-            G, rse_e2e, _ = decompose(Xh, K, R, "als", args.prec, 1903, sweeps, init=pipe.init, engine=pipe.eng)
+        res = decompose_stream([Xh] * ek, K, R, "als", args.prec, 1903, sweeps, init=pipe.init, engines=engs)
         el = time.perf_counter() - t
-        d2h = sum(g.numel() * 8 for g in G) + 8
+        d2h = sum(g.numel() * 8 for g in res[-1][0]) + 8
         out["e2e"] = {"value": round(world * xbytes * ek / el / 1e9, 3), "unit": "GB/s",
                       "h2d_bytes_per_step": int(xbytes), "d2h_bytes_per_step": int(d2h),
-                      "ms_per_step": round(el / ek * 1e3, 3)}
+                      "ms_per_step": round(el / ek * 1e3, 3), "inflight": inflight}
         del Xh
+        X = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle leg: the oracle timed on the host cores, and the 1e-3 gate
         # of the metric checked against it on a tensor that runs the same kernels
-        del X
+        X = None
         torch.cuda.empty_cache()
         out["cpu_baseline"] = cpu_baseline()
         if not args.no_parity:

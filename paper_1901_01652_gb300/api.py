@@ -108,3 +108,42 @@ def decompose(X_host, K, R, method="als", prec="fp32", seed=0, sweeps=20, tol=1e
     rse = eng.rse.to("cpu", non_blocking=True)
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     return G, float(rse[0]), eng
+
+
+def decompose_stream(X_hosts, K, R, method="als", prec="fp32", seed=0, sweeps=20, tol=1e-2, init=None,
+                     engines=None, inflight=2):
+    """End to end for a sequence of host tensors of one shape: per tensor the
+    H2D copy of X, Algorithm 1 on the GPU, and the D2H copies of the cores G_n
+    and the RSE.  Consecutive tensors alternate over `inflight` engines (each
+    its own plan, device copy of X and stream), so that one tensor's copies
+    and TR-ALS overlap the next one's sketch.  Page-locked host tensors let
+    the copies run asynchronously.  `engines`: RTRD objects to reuse (one per
+    tensor in flight).  Returns [(G, rse)] in input order."""
+    if not X_hosts:
+        return []
+    dims = tuple(X_hosts[0].shape)
+    engs = list(engines) if engines is not None else \
+        [RTRD(dims, K, R, prec, seed, sweeps, tol) for _ in range(max(1, inflight))]
+    n = len(engs)
+    streams = [torch.cuda.Stream(e.device) for e in engs]
+    bufs = [torch.empty(dims, dtype=e.plan.x_dtype, device=e.device) for e in engs]
+    main = torch.cuda.current_stream(engs[0].device)
+    for st in streams:
+        st.wait_stream(main)
+    out = []
+    for i, Xh in enumerate(X_hosts):
+        k = i % n
+        eng, st, Xd = engs[k], streams[k], bufs[k]
+        with torch.cuda.stream(st):
+            Xd.copy_(Xh, non_blocking=True)
+            eng.run(Xd, method, init, stream=st)
+            eng.compute_rse(st)
+            G = [torch.empty(g.shape, dtype=g.dtype, pin_memory=True) for g in eng.cores()]
+            for g, gd in zip(G, eng.cores()):
+                g.copy_(gd, non_blocking=True)
+            rse = torch.empty(1, dtype=torch.float64, pin_memory=True)
+            rse.copy_(eng.rse, non_blocking=True)
+        out.append((G, rse))
+    for st in streams:
+        st.synchronize()
+    return [(G, float(r[0])) for G, r in out]

@@ -174,3 +174,58 @@ def label_targets(labels, shapes):
             T[t, 2 * n + 1] = int(R) / 16.0
             M[t, 2 * n] = M[t, 2 * n + 1] = 1.0
     return T, M
+
+
+def nested_rank_sweep(X, S, R_values, target=1e-2, prec="fp32", seed=0, sweeps=10):
+    """Rank-sweep label of one tensor with few sketches (the prefix reuse of
+    the sketch sizes) and every TR-ALS run on the small projected tensor only;
+    the result is rank_sweep_labels' for a tensor decomposed with `seed`.
+
+    R uses K_n = min(I_n, k_rule(R)).  A mode with k_rule(R) >= I_n is kept
+    whole, so the R values are grouped by the set of projected modes (larger
+    R keep more modes whole).  Within a group the test matrix of a smaller K
+    is the first K columns of the group's largest one (Omega_n[r, k] depends on
+    (r, k) only), its basis the first K columns of the largest basis (QR is
+    nested in its columns), and its projection P_K the leading block of the
+    largest projection.  So per group X is sketched and projected once and S
+    (the clean signal) projected with the same bases; for every R the grouped
+    TR-ALS of the batched form runs on P_K alone (the solver and start of
+    rank_sweep_labels), and the error against the clean signal is
+        ||Xhat - S||^2 = ||TR(Z)||^2 - 2 <TR(Z), P_S,K> + ||S||^2
+    with Xhat = TR(Z) x_n Q_K (Eq. 3; Q_K orthonormal).
+    Returns (label R, error per R)."""
+    from .api import RTRD
+    dims = tuple(X.shape)
+    N = len(dims)
+    nS2 = float(torch.linalg.vector_norm(S, dtype=torch.float64)) ** 2
+    groups = {}
+    for R in R_values:
+        groups.setdefault(tuple(k_rule(R) < d for d in dims), []).append(R)
+    errs = {}
+    for pattern, Rg in groups.items():
+        Kg = [max(k_rule(R) for R in Rg) if pr else d for pr, d in zip(pattern, dims)]
+        eng = RTRD(dims, Kg, [1] * N, prec, seed, sweeps, device=X.device)
+        eng.sketch(X)
+        eng.project(X)
+        PS = torch.empty_like(eng.P)
+        rtr.rtr_project(eng.plan, S, eng.Y, [torch.empty_like(q) for q in eng.Q], PS)
+        for R in Rg:
+            idx = tuple(slice(0, min(d, k_rule(R))) for d in dims)
+            PK, PSK = eng.P[idx].contiguous(), PS[idx].contiguous()
+            K = tuple(PK.shape)
+            Rl = (R,) * N
+            params = rtr.make_params(prec, seed, sweeps)
+            params.flags = rtr.PARAM_NO_GRAPH
+            b = rtr.rtr_batch_create([K], [K], [Rl], params, 1)
+            G = [torch.empty(R * k * R, dtype=torch.float64, device=X.device) for k in K]
+            rtr.rtr_batch_run(b, [PK], [G], None)
+            work = torch.empty(rtr.rtr_reconstruct_work_bytes(K, Rl), dtype=torch.uint8, device=X.device)
+            T = torch.empty(K, dtype=torch.float64, device=X.device)
+            rtr.rtr_reconstruct(K, Rl, G, "fp64", T, work)
+            e2 = float((T * T).sum()) - 2.0 * float((T * PSK.double()).sum()) + nS2
+            errs[R] = max(e2, 0.0) ** 0.5 / nS2 ** 0.5
+            b.close()
+        eng.plan.close()
+    errs = np.array([errs[R] for R in R_values])
+    ok = np.nonzero(errs <= target)[0]
+    return (R_values[ok[0]] if ok.size else R_values[-1]), errs
