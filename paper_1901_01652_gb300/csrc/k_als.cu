@@ -122,14 +122,14 @@ __global__ void trace_kernel(const double* __restrict__ M, int n, double* __rest
     }
 }
 
-// Mprod = E_{s} E_{s+1} ... (cyclic, cnt factors), one CTA per output row:
-// the row is carried through the chain in shared memory (float64); each
-// product splits the sum over l across 8 thread slices (independent load
-// chains), reduced in shared memory in a fixed order.
+// Mprod = F_0 F_1 ... F_{cnt-1} (F_t: dim[t] x dim[t+1], float64), one CTA
+// per output row: the row is carried through the chain in shared memory;
+// each product splits the sum over l across 8 thread slices (independent
+// load chains), reduced in shared memory in a fixed order.
 struct GramChainArgs {
-    const double* E[RTR_MAXN];
-    int R[RTR_MAXN];
-    int N, start, cnt;
+    const double* F[RTR_MAXN];
+    int dim[RTR_MAXN + 1];
+    int cnt;
     double* out;
     float* outf;              // optional float32 copy of out (converted here, on 100 SMs, not
                               // in the single-CTA kernels: float64 conversions are slow)
@@ -143,16 +143,14 @@ __global__ void __launch_bounds__(GC_THREADS) gram_chain_kernel(const GramChainA
     __shared__ double part[8][GC_COLS];
     const int r = blockIdx.x;
     const int tid = threadIdx.x, jl = tid % GC_COLS, q = tid / GC_COLS;
-    int m = g.start % g.N;
-    int len = g.R[(m + 1) % g.N] * g.R[(m + 1) % g.N];
-    for (int j = tid; j < len; j += blockDim.x) v0[j] = g.E[m][(int64_t)r * len + j];
+    int len = g.dim[1];
+    for (int j = tid; j < len; j += blockDim.x) v0[j] = g.F[0][(int64_t)r * len + j];
     double* cur = v0;
     double* nxt = v1;
     for (int t = 1; t < g.cnt; ++t) {
         __syncthreads();
-        m = (g.start + t) % g.N;
-        const int cols = g.R[(m + 1) % g.N] * g.R[(m + 1) % g.N];
-        const double* Em = g.E[m];
+        const int cols = g.dim[t + 1];
+        const double* Em = g.F[t];
         for (int j0 = 0; j0 < cols; j0 += GC_COLS) {
             const int j = j0 + jl;
             double s = 0.0;
@@ -671,6 +669,276 @@ inline unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 65535) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(rtr_ceil_div(n, threads), cap));
 }
 
+// ---- fused subchain and contraction (float32 plans) --------------------------
+// W = P_<n> S_{!=n} (Eq. 2 and the update below it) without storing the
+// subchain S: its slice for the other modes' indices j is the matrix product
+// Z_{n+1}(j_{n+1}) ... Z_{n-1}(j_{n-1}) (R_{n+1} x R_n), and
+//     W[i, be R_n + g] = sum_j P[.., i, ..](j) S(j)[be, g].
+// The chain's cores before the last one are the "outer" modes, the last core
+// (mode n-1) the "inner" one.  A CTA takes a contiguous range of outer
+// multi-indices o in batches of up to gb; per batch it forms, in shared
+// memory, M(o) = Z_{n+1}(j_{n+1}) ... Z_{n-2}(j_{n-2}), the slices
+// S(o, l) = M(o) Z_{n-1}(l) for every inner index l, and the K_n x K_{n-1}
+// blocks of P that meet them, then adds the block products to float32
+// accumulators: a thread owns a 4 x 4 tile of W (4 rows i, 4 columns) and
+// reads 4 + 4 values per 16 FMAs.  The products associate as in the stored
+// subchain ((Z_{n+1} Z_{n+2}) Z_{n+3} ...).  Each CTA writes its partial W in
+// float64; fused_reduce_kernel sums the partials in a fixed order.
+constexpr int FC_THREADS = 256;
+constexpr int FC_MAXB = 8;           // outer indices per batch
+
+struct FusedContractArgs {
+    const float* P;
+    const float* Z[RTR_MAXN];   // chain order: Z[t] = core (n + 1 + t) mod N
+    int R[RTR_MAXN + 1];        // R[t] x K[t] x R[t + 1] = shape of Z[t]; R[0] = R_{n+1}, R[L] = R_n
+    int K[RTR_MAXN];
+    int64_t st[RTR_MAXN];       // stride in P of chain core t's index
+    int L;                      // chain length N - 1 (>= 2)
+    int Kn;                     // K_n
+    int64_t stn;                // stride in P of mode n
+    int64_t nouter;             // product of K[0 .. L-2]
+    int C, C4, Kn4, Rn4;        // R_{n+1} R_n, and C, K_n, R_n rounded up to multiples of 4
+    int gb;                     // outer indices per batch (<= FC_MAXB)
+    double* partial;            // gridDim.x x (K_n C)
+};
+
+template <int NT>
+__global__ void __launch_bounds__(FC_THREADS) fused_contract_kernel(const FusedContractArgs a) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ int64_t off_s[FC_MAXB];
+    __shared__ int jo_s[FC_MAXB][RTR_MAXN];
+    const int L = a.L, KL = a.K[L - 1], Rl = a.R[L - 1], Rn = a.R[L], R0 = a.R[0];
+    const int C = a.C, C4 = a.C4, Kn = a.Kn, Kn4 = a.Kn4, Rn4 = a.Rn4, GB = a.gb;
+    float* zl = fsm;                                   // inner core, Rl x KL x Rn4 (g >= Rn zero)
+    float* mb = zl + Rl * KL * Rn4;                    // 2 x GB x 256: M of each outer index
+    float* Pb = mb + 2 * GB * 256;                     // GB x KL x Kn4: P blocks, i fastest
+    float* Sb = Pb + GB * KL * Kn4;                    // GB x KL x C4: slices of S
+    const int tid = threadIdx.x;
+    for (int e = tid; e < Rl * KL * Rn4; e += FC_THREADS) {
+        const int g = e % Rn4, hl = e / Rn4;
+        zl[e] = g < Rn ? a.Z[L - 1][(int64_t)hl * Rn + g] : 0.f;
+    }
+    const int64_t per = a.nouter / gridDim.x, rem = a.nouter % gridDim.x;
+    const int64_t o0 = blockIdx.x * per + min((int64_t)blockIdx.x, rem);
+    const int64_t o1 = o0 + per + ((int64_t)blockIdx.x < rem ? 1 : 0);
+    const int ti4 = Kn4 >> 2, tc4 = C4 >> 2, ntile = ti4 * tc4;
+    float acc[NT][4][4];
+#pragma unroll
+    for (int q = 0; q < NT; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[q][u][0] = acc[q][u][1] = acc[q][u][2] = acc[q][u][3] = 0.f;
+
+    for (int64_t ob = o0; ob < o1; ob += GB) {
+        const int gb = (int)min((int64_t)GB, o1 - ob);
+        __syncthreads();                               // the previous batch's readers are done
+        if (tid < gb) {
+            int64_t off = 0, rest = ob + tid;
+            for (int t = L - 2; t >= 0; --t) {
+                const int j = (int)(rest % a.K[t]);
+                rest /= a.K[t];
+                jo_s[tid][t] = j;
+                off += (int64_t)j * a.st[t];
+            }
+            off_s[tid] = off;
+        }
+        __syncthreads();
+        // P blocks (the inner index fastest in the reads), i fastest in shared memory
+        for (int e = tid; e < gb * Kn4 * KL; e += FC_THREADS) {
+            const int l = e % KL, r = e / KL, i = r % Kn4, b = r / Kn4;
+            Pb[(b * KL + l) * Kn4 + i] = i < Kn ? a.P[off_s[b] + (int64_t)l * a.st[L - 1] + (int64_t)i * a.stn] : 0.f;
+        }
+        // M(o) = Z[0](j_0) ... Z[L-2](j_{L-2})   (R0 x Rl)
+        int mw = 0;
+        {
+            const int R1 = a.R[1];
+            for (int e = tid; e < gb * R0 * R1; e += FC_THREADS) {
+                const int b = e / (R0 * R1), rc = e - b * R0 * R1, r = rc / R1, c = rc - r * R1;
+                mb[b * 256 + rc] = a.Z[0][((int64_t)r * a.K[0] + jo_s[b][0]) * R1 + c];
+            }
+            for (int t = 1; t < L - 1; ++t) {
+                __syncthreads();
+                const int Rt = a.R[t], Rt1 = a.R[t + 1];
+                const float* cur = mb + mw * GB * 256;
+                float* nxt = mb + (mw ^ 1) * GB * 256;
+                for (int e = tid; e < gb * R0 * Rt1; e += FC_THREADS) {
+                    const int b = e / (R0 * Rt1), rc = e - b * R0 * Rt1, r = rc / Rt1, c = rc - r * Rt1;
+                    float v = 0.f;
+                    for (int h = 0; h < Rt; ++h)
+                        v = fmaf(cur[b * 256 + r * Rt + h], a.Z[t][((int64_t)h * a.K[t] + jo_s[b][t]) * Rt1 + c], v);
+                    nxt[b * 256 + rc] = v;
+                }
+                mw ^= 1;
+            }
+        }
+        __syncthreads();
+        // S(o, l)[be, g] = sum_h M(o)[be, h] Z_{n-1}[h, l, g]: a thread per (o, l, be)
+        // keeps the R_n sums of its row in registers
+        const float* M = mb + mw * GB * 256;
+        for (int e = tid; e < gb * KL * R0; e += FC_THREADS) {
+            const int be = e % R0, bl = e / R0, l = bl % KL, b = bl / KL;
+            float v[16];
+#pragma unroll
+            for (int g = 0; g < 16; ++g) v[g] = 0.f;
+            for (int h = 0; h < Rl; ++h) {
+                const float mv = M[b * 256 + be * Rl + h];
+                const float4* zr = reinterpret_cast<const float4*>(zl + (h * KL + l) * Rn4);
+#pragma unroll
+                for (int g4 = 0; g4 < 4; ++g4)
+                    if (4 * g4 < Rn) {
+                        const float4 z = zr[g4];
+                        v[4 * g4] = fmaf(mv, z.x, v[4 * g4]); v[4 * g4 + 1] = fmaf(mv, z.y, v[4 * g4 + 1]);
+                        v[4 * g4 + 2] = fmaf(mv, z.z, v[4 * g4 + 2]); v[4 * g4 + 3] = fmaf(mv, z.w, v[4 * g4 + 3]);
+                    }
+            }
+            float* so = Sb + bl * C4 + be * Rn;
+#pragma unroll
+            for (int g = 0; g < 16; ++g)
+                if (g < Rn) so[g] = v[g];
+        }
+        if (C4 > C)
+            for (int e = tid; e < gb * KL * (C4 - C); e += FC_THREADS)
+                Sb[(e / (C4 - C)) * C4 + C + e % (C4 - C)] = 0.f;
+        __syncthreads();
+        // acc[tile] += sum over (o, l) of Pb[o, l, i0 .. i0 + 3]^T Sb[o, l, c0 .. c0 + 3]
+        const int nk = gb * KL;
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int tl = tid + FC_THREADS * q;
+            if (NT > 1 && tl >= ntile) break;
+            if (tl < ntile) {
+                const int i0 = 4 * (tl / tc4), c0 = 4 * (tl % tc4);
+                const float* pa = Pb + i0;
+                const float* sa = Sb + c0;
+#pragma unroll 4
+                for (int k = 0; k < nk; ++k) {
+                    const float4 pv = *reinterpret_cast<const float4*>(pa + k * Kn4);
+                    const float4 sv = *reinterpret_cast<const float4*>(sa + k * C4);
+                    const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        acc[q][u][0] = fmaf(pp[u], sv.x, acc[q][u][0]);
+                        acc[q][u][1] = fmaf(pp[u], sv.y, acc[q][u][1]);
+                        acc[q][u][2] = fmaf(pp[u], sv.z, acc[q][u][2]);
+                        acc[q][u][3] = fmaf(pp[u], sv.w, acc[q][u][3]);
+                    }
+                }
+            }
+        }
+    }
+    double* dst = a.partial + (int64_t)blockIdx.x * Kn * C;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+        const int tl = tid + FC_THREADS * q;
+        if (tl < ntile) {
+            const int i0 = 4 * (tl / tc4), c0 = 4 * (tl % tc4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (i0 + u < Kn && c0 + w < C) dst[(int64_t)(i0 + u) * C + c0 + w] = (double)acc[q][u][w];
+        }
+    }
+}
+
+// W[e] = sum of the partials: thread (g, x) of a CTA adds partials g, g + 8,
+// ... of output e = 32 blockIdx.x + x (consecutive x: consecutive addresses),
+// then the 8 group sums are added in order (the result does not depend on timing)
+__global__ void __launch_bounds__(256) fused_reduce_kernel(const double* __restrict__ partial, int nparts, int count,
+                                                           double* __restrict__ W) {
+    __shared__ double red[8][33];
+    const int x = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + x;
+    double s = 0.0;
+    if (e < count)
+        for (int q = g; q < nparts; q += 8) s += partial[(int64_t)q * count + e];
+    red[g][x] = s;
+    __syncthreads();
+    if (g == 0 && e < count) {
+        double t = red[0][x];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) t += red[u][x];
+        W[e] = t;
+    }
+}
+
+// shared memory of the fused contraction for batches of gb outer indices
+size_t fused_contract_smem(int N, const int64_t* Kd, const int* R, int n, int gb) {
+    const int m_last = (n + N - 1) % N;
+    const size_t KL = (size_t)Kd[m_last], Rl = (size_t)R[m_last];
+    const size_t Rn4 = (size_t)((R[n] + 3) & ~3), Kn4 = (size_t)((Kd[n] + 3) & ~3);
+    const size_t C4 = (size_t)((R[(n + 1) % N] * R[n] + 3) & ~3);
+    return sizeof(float) * (Rl * KL * Rn4 + 2 * (size_t)gb * 256 + (size_t)gb * KL * (Kn4 + C4));
+}
+
+constexpr size_t FC_SMEM_LIMIT = 200 * 1024;
+
+// 0 if the fused form applies (every size within its shared memory and
+// register tiling), else nonzero (the caller keeps the stored subchain then)
+int fused_contract_ok(rtr_plan* p, int n) {
+    const int N = p->N;
+    int64_t Kd[RTR_MAXN];
+    for (int m = 0; m < N; ++m) Kd[m] = p->K[m];
+    if (N < 3) return 1;
+    for (int m = 0; m < N; ++m) if (p->R[m] > 16) return 1;
+    const int C4 = (p->R[(n + 1) % N] * p->R[n] + 3) & ~3;
+    const int ntile = (int)(((Kd[n] + 3) & ~3) >> 2) * (C4 >> 2);
+    if (ntile > 4 * FC_THREADS) return 1;
+    if (fused_contract_smem(N, Kd, p->R, n, 1) > FC_SMEM_LIMIT) return 1;
+    return 0;
+}
+
+int launch_fused_contract(rtr_plan* p, const float* P, const float* const* Zf, int n, double* W, cudaStream_t s) {
+    const int N = p->N;
+    int64_t Kd[RTR_MAXN];
+    for (int m = 0; m < N; ++m) Kd[m] = p->K[m];
+    FusedContractArgs a{};
+    a.P = P;
+    a.L = N - 1;
+    int64_t stride[RTR_MAXN];
+    stride[N - 1] = 1;
+    for (int m = N - 2; m >= 0; --m) stride[m] = stride[m + 1] * Kd[m + 1];
+    for (int t = 0; t < a.L; ++t) {
+        const int m = (n + 1 + t) % N;
+        a.Z[t] = Zf[m];
+        a.R[t] = p->R[m];
+        a.K[t] = (int)Kd[m];
+        a.st[t] = stride[m];
+    }
+    a.R[a.L] = p->R[n];
+    a.Kn = (int)Kd[n];
+    a.stn = stride[n];
+    a.nouter = 1;
+    for (int t = 0; t + 1 < a.L; ++t) a.nouter *= a.K[t];
+    a.C = p->R[(n + 1) % N] * p->R[n];
+    a.C4 = (a.C + 3) & ~3;
+    a.Kn4 = (a.Kn + 3) & ~3;
+    a.Rn4 = (p->R[n] + 3) & ~3;
+    const int count = a.Kn * a.C;
+    int64_t gx = std::min<int64_t>(a.nouter, (int64_t)p->num_sms);
+    gx = std::min<int64_t>(gx, (int64_t)(p->partial_elems / (size_t)count));
+    if (gx < 1) return rtr_set_error(RTR_ENOMEM, "TR-ALS: contraction partials exceed the plan workspace");
+    // one batch per CTA where shared memory allows
+    int gb = (int)std::min<int64_t>(FC_MAXB, rtr_ceil_div(a.nouter, gx));
+    while (gb > 1 && fused_contract_smem(N, Kd, p->R, n, gb) > FC_SMEM_LIMIT) --gb;
+    a.gb = gb;
+    a.partial = p->partial;
+    const size_t smem = fused_contract_smem(N, Kd, p->R, n, gb);
+    const int ntile = (a.Kn4 >> 2) * (a.C4 >> 2);
+    const int nt = (ntile + FC_THREADS - 1) / FC_THREADS;
+#define RTR_FC(NT_)                                                                                       \
+    if (nt <= NT_) {                                                                                      \
+        RTR_CUDA(cudaFuncSetAttribute(fused_contract_kernel<NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem));                                                        \
+        fused_contract_kernel<NT_><<<(unsigned)gx, FC_THREADS, smem, s>>>(a);                             \
+    } else
+    RTR_FC(1) RTR_FC(2) RTR_FC(4) { return rtr_set_error(RTR_EINVAL, "TR-ALS: fused contraction too wide"); }
+#undef RTR_FC
+    RTR_LAUNCH_CHECK("fused_contract_kernel");
+    fused_reduce_kernel<<<(unsigned)rtr_ceil_div(count, 32), 256, 0, s>>>(p->partial, (int)gx, count, W);
+    RTR_LAUNCH_CHECK("fused_reduce_kernel");
+    return RTR_OK;
+}
+
 // Build subchain products over `cores` in ring order start, start+1, ...,
 // start+count-1 (indices mod N); writes the product slices for every
 // multi-index (row-major) as rows x Rfirst x Rlast into one of two buffers,
@@ -735,12 +1003,14 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     double* E[RTR_MAXN];
     for (int n = 0; n < N; ++n) E[n] = ws + n * ESZ;
     double* Mp[2] = {ws + RTR_MAXN * ESZ, ws + (RTR_MAXN + 1) * ESZ};
+    // prefix products A_n = E_{n+1} ... E_{n-2} of the Gram chains (ping-pong)
+    double* Ab[2] = {ws + (RTR_MAXN + 2) * ESZ, ws + (RTR_MAXN + 3) * ESZ};
     // Mp[1] serves the start's transfer products only; during the sweeps it
     // holds the float32 inverse of the current Gram matrix
     float* Ginv = reinterpret_cast<float*>(Mp[1]);
     float* Gf = Ginv + 160 * 160;                    // float32 copy of the Gram matrix (hi part)
     float* Gfl = Gf + 160 * 160;                     // and its low part
-    double* W = ws + (RTR_MAXN + 2) * ESZ;
+    double* W = ws + (RTR_MAXN + 4) * ESZ;
     double* Wz = W + p->als_wmax;
     double* jac = Wz + p->als_wmax;              // 2 * 144^2 for the pinv fallback
     double* zw = jac + 2 * 144 * 144;            // z_i . w_i per slice (max K_n)
@@ -819,7 +1089,40 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     } else {
         for (int n = 0; n < N; ++n) Zt[n] = Z[n];
     }
-    cudaStream_t side = p->side;
+    cudaStream_t side = p->side, side2 = p->side2;
+    // The Gram matrix of update n is G_n = A_n E_{n-1} (reindexed) with the
+    // prefix A_n = E_{n+1} ... E_{n-2}, which does not involve the core updated
+    // last: A_{n+1} is formed on a third stream during update n, as soon as
+    // E_{n-1} is known, so that update n + 1's side chain holds one product.
+    // (Order 3: A_n = E_{n+1}, no product.)
+    // buf: the update's running number modulo 2 (consecutive updates alternate)
+    auto prefix = [&](int n1, int buf, cudaStream_t st, double** res) -> int {
+        if (N == 3) { *res = E[(n1 + 1) % N]; return RTR_OK; }
+        GramChainArgs ga{};
+        ga.cnt = N - 2;
+        for (int t = 0; t < ga.cnt; ++t) {
+            const int m = (n1 + 1 + t) % N;
+            ga.F[t] = E[m];
+            ga.dim[t] = p->R[m] * p->R[m];
+        }
+        const int ml = (n1 + N - 1) % N;
+        ga.dim[ga.cnt] = p->R[ml] * p->R[ml];
+        ga.out = Ab[buf];
+        const int rows = p->R[(n1 + 1) % N] * p->R[(n1 + 1) % N];
+        gram_chain_kernel<<<(unsigned)rows, GC_THREADS, 0, st>>>(ga);
+        RTR_LAUNCH_CHECK("gram_chain_kernel");
+        *res = Ab[buf];
+        return RTR_OK;
+    };
+    double* Acur = nullptr;
+    // A_0 of the first update, from the start's transfer matrices
+    RTR_CUDA(cudaEventRecord(p->ev[4], s));
+    RTR_CUDA(cudaStreamWaitEvent(side2, p->ev[4], 0));
+    if ((st = prefix(0, 0, side2, &Acur))) return st;
+    RTR_CUDA(cudaEventRecord(p->ev[5], side2));
+    // the float plans form W without storing the subchain where the sizes allow
+    int fused[RTR_MAXN] = {};
+    for (int n = 0; n < N; ++n) fused[n] = !is_f64 && fused_contract_ok(p, n) == 0;
     // dynamic shared memory limits, set once for the largest update (a host
     // API call per launch would pace the whole chain of small kernels)
     {
@@ -834,26 +1137,37 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             const int C = Rn * Rn1;
             int64_t A, I, B;
             rtr_mode_view(N, Kd, n, &A, &I, &B);
-            // ---- side stream: E of the core updated last, then G = E_{n+1} ... E_{n-1}
+            // ---- side stream: E of the core updated last, then G = A_n E_{n-1}
             RTR_CUDA(cudaEventRecord(p->ev[0], s));
             RTR_CUDA(cudaStreamWaitEvent(side, p->ev[0], 0));
+            const int ml = (n + N - 1) % N;
             if (sweep > 0 || n > 0) {
-                const int m = (n + N - 1) % N;
-                const int Ra = p->R[m], Rb = p->R[(m + 1) % N];
+                const int Ra = p->R[ml], Rb = p->R[(ml + 1) % N];
                 // 64-thread blocks: the float64 work spreads over every SM
-                transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb, 64), 64, 0, side>>>(Z[m], Ra, (int)Kd[m], Rb, E[m]);
+                transfer_kernel<<<grid_for((int64_t)Ra * Ra * Rb * Rb, 64), 64, 0, side>>>(Z[ml], Ra, (int)Kd[ml], Rb, E[ml]);
                 RTR_LAUNCH_CHECK("transfer_kernel");
             }
+            RTR_CUDA(cudaEventRecord(p->ev[4], side));
+            RTR_CUDA(cudaStreamWaitEvent(side, p->ev[5], 0));     // A_n formed
             GramChainArgs gc{};
-            for (int m = 0; m < N; ++m) { gc.E[m] = E[m]; gc.R[m] = p->R[m]; }
-            gc.N = N; gc.start = n + 1; gc.cnt = N - 1; gc.out = Mp[0];
+            gc.cnt = 2;
+            gc.F[0] = Acur; gc.F[1] = E[ml];
+            gc.dim[0] = Rn1 * Rn1; gc.dim[1] = p->R[ml] * p->R[ml]; gc.dim[2] = Rn * Rn;
+            gc.out = Mp[0];
             gc.reindex = 1; gc.Rb = Rn1; gc.Rn = Rn; gc.outf = Gf; gc.outl = Gfl;
             gram_chain_kernel<<<(unsigned)(Rn1 * Rn1), GC_THREADS, 0, side>>>(gc);
             RTR_LAUNCH_CHECK("gram_chain_kernel");
             if ((st = launch_gram_inverse(Gf, C, Ginv, need_slow, side))) return st;
             RTR_CUDA(cudaEventRecord(p->ev[1], side));
+            // ---- third stream: A_{n+1} for the next update, once E_{n-1} is known
+            RTR_CUDA(cudaStreamWaitEvent(side2, p->ev[4], 0));
+            if ((st = prefix((n + 1) % N, (sweep * N + n + 1) & 1, side2, &Acur))) return st;
+            RTR_CUDA(cudaEventRecord(p->ev[5], side2));
             // ---- caller's stream: W = P_<n> S, subchain generated in the contraction
             // ---- caller's stream: subchain S (natural row order), then W = P_<n> S
+            if (!is_f64 && fused[n]) {
+                if ((st = launch_fused_contract(p, reinterpret_cast<const float*>(P), Zf, n, W, s))) return st;
+            } else {
             if ((size_t)(A * B) * (size_t)C * sizeof(T) > p->sub_bytes)
                 return rtr_set_error(RTR_ENOMEM, "TR-ALS: subchain exceeds the plan workspace");
             const T* Zc[RTR_MAXN];
@@ -868,6 +1182,7 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
                 w.gen = 0; w.M = Sn; w.ldm = C;
                 w.Y = W; w.norm_out = nullptr;
                 if ((st = launch_contract(p, is_f64, w, s))) return st;
+            }
             }
             // ---- join, then solve G z_i = w_i for every slice
             RTR_CUDA(cudaStreamWaitEvent(s, p->ev[1], 0));
@@ -889,6 +1204,8 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
             }
         }
     }
+    // the last prefix product (for an update that does not come) joins the caller's stream
+    RTR_CUDA(cudaStreamWaitEvent(s, p->ev[5], 0));
     return RTR_OK;
 }
 

@@ -118,10 +118,11 @@ void free_plan(rtr_plan* p) {
     cudaFree(p->qr_ws); cudaFree(p->als_ws); cudaFree(p->sub_ws[0]);
     cudaFree(p->flags); cudaFree(p->tc_ws); cudaFree(p->svd_ws); cudaFree(p->ttm_q);
     cudaFree(p->pow_q); cudaFree(p->pow_t); cudaFree(p->acc_y);
-    for (int e = 0; e < 4; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
+    for (int e = 0; e < 6; ++e) if (p->ev[e]) cudaEventDestroy(p->ev[e]);
     if (p->als_exec) cudaGraphExecDestroy(p->als_exec);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->side) cudaStreamDestroy(p->side);
+    if (p->side2) cudaStreamDestroy(p->side2);
     delete p;
 }
 
@@ -305,7 +306,7 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
         core_elems += (((int64_t)R[n] * p->K[n] * R[(n + 1) % N]) + 3) & ~(int64_t)3;
     }
     p->als_maxK = (size_t)maxK;
-    p->als_ws_elems = (size_t)(RTR_MAXN + 2) * 256 * 256 + 2 * p->als_wmax + 2 * 144 * 144 + (size_t)maxK +
+    p->als_ws_elems = (size_t)(RTR_MAXN + 4) * 256 * 256 + 2 * p->als_wmax + 2 * 144 * 144 + (size_t)maxK +
                       (size_t)(core_elems / 2 + 8);   // float32 core shadows
     RTR_TRY(dalloc(&p->als_ws, p->als_ws_elems));
     {
@@ -315,7 +316,8 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
     }
     RTR_TRYC(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     RTR_TRYC(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
-    for (int e = 0; e < 4; ++e) RTR_TRYC(cudaEventCreateWithFlags(&p->ev[e], cudaEventDisableTiming));
+    RTR_TRYC(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking));
+    for (int e = 0; e < 6; ++e) RTR_TRYC(cudaEventCreateWithFlags(&p->ev[e], cudaEventDisableTiming));
     RTR_TRY(dalloc(&p->flags, 4));
     RTR_TRYC(cudaMemset(p->flags, 0, 4 * sizeof(int)));
     RTR_TRY(dalloc(&p->svd_ws, trsvd_ws_elems(p->pnumel, &p->svd_cbuf, &p->svd_gmax, &p->svd_umax)));

@@ -40,7 +40,8 @@ struct rtr_plan {
     size_t als_wmax = 0;         // max K_n R_n R_{n+1}
     size_t als_maxK = 0;         // max K_n
     cudaStream_t side = nullptr; // second stream for work that overlaps the caller's stream
-    cudaEvent_t ev[4] = {};
+    cudaStream_t side2 = nullptr;// third stream (TR-ALS: prefix products of the Gram chains)
+    cudaEvent_t ev[6] = {};
     // TR-ALS replay: the sweeps of rtr_als recorded once (on `cap`, a stream of
     // the plan) per argument set and replayed on the caller's stream
     cudaStream_t cap = nullptr;

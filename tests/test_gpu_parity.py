@@ -238,6 +238,27 @@ def test_als_fp32_contraction_vs_oracle():
     assert np.max(np.abs(err - np.array(errs)) / np.array(errs)) < 1e-3
 
 
+@pytest.mark.parametrize("dims,R", [
+    ((12, 11, 13), (2, 3, 5)),                # order 3 (one outer core): R_{n+1} R_n = 15, 10, 6
+    ((9, 8, 7, 10, 6), (2, 3, 2, 3, 1)),      # order 5: three outer cores per update
+    ((40, 33, 37, 35), (12, 6, 9, 7)),        # K_n up to 40, R_{n+1} R_n up to 108 (eight items a thread)
+    ((64, 20, 64, 5), (4, 16, 4, 3)),         # K_n = 64, R = 16
+])
+def test_als_fp32_fused_contraction_orders(dims, R):
+    """The float32 plans form W = P_<n> S without storing the subchain; the
+    TR-ALS result follows the oracle's for orders 3-5 and rank products
+    that are not multiples of 4."""
+    P32 = noisy_tr(dims, R, 30.0, 16).astype(np.float32)
+    init = workloads.als_init(dims, R, 17)
+    sweeps = 3
+    plan = make_plan(dims, dims, R, "fp32", sweeps=sweeps)
+    Z, err = run_als(plan, P32, init, sweeps)
+    assert rtr.rtr_plan_flags(plan) & ~rtr.FLAG_GRAM_PINV == 0
+    Zr, errs = orc.tr_als(P32.astype(np.float64), R, sweeps, init=init)
+    assert rel(ot.tr_full(Z), ot.tr_full(Zr)) < 1e-4
+    assert np.max(np.abs(err - np.array(errs)) / np.array(errs)) < 1e-3
+
+
 # ------------------------------------------------------------------ back-projection, Psi, RSE
 
 def test_backproject_and_reconstruct_vs_oracle():
