@@ -45,9 +45,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-parity", action="store_true", help="skip the reduced-tensor parity check vs the oracle")
-    ap.add_argument("--inflight", type=int, default=2,
+    ap.add_argument("--inflight", type=int, default=4,
                     help="tensors in flight: consecutive steps on this many streams, each with its own plan, so that "
-                         "one tensor's TR-ALS overlaps the next one's sketch (1 = one step after the other)")
+                         "the latency-bound TR-ALS runs of several tensors overlap one another and the HBM-bound "
+                         "passes of the others (1 = one step after the other)")
     ap.add_argument("--workload", default="c2", choices=["c2", "batch256", "c1", "c3"],
                     help="c2 = the 200^4 tensor (default); batch256 = 256 uneven image-like tensors; "
                          "c1 = FP64 60^4 TR-ALS; c3 = hyperspectral-shaped 1024x1024x256 TR-SVD")
