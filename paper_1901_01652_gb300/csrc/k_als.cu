@@ -927,8 +927,7 @@ int launch_fused_contract(rtr_plan* p, const float* P, const float* const* Zf, i
     const int nt = (ntile + FC_THREADS - 1) / FC_THREADS;
 #define RTR_FC(NT_)                                                                                       \
     if (nt <= NT_) {                                                                                      \
-        RTR_CUDA(cudaFuncSetAttribute(fused_contract_kernel<NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                      (int)smem));                                                        \
+        RTR_SMEM(fused_contract_kernel<NT_>, smem);                                                        \
         fused_contract_kernel<NT_><<<(unsigned)gx, FC_THREADS, smem, s>>>(a);                             \
     } else
     RTR_FC(1) RTR_FC(2) RTR_FC(4) { return rtr_set_error(RTR_EINVAL, "TR-ALS: fused contraction too wide"); }
@@ -1128,8 +1127,7 @@ int als_impl(rtr_plan* p, const T* P, double* const* Z, int init_given, double* 
     {
         int cmax = 0;
         for (int n = 0; n < N; ++n) cmax = std::max(cmax, p->R[n] * p->R[(n + 1) % N]);
-        RTR_CUDA(cudaFuncSetAttribute(als_solve_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * (size_t)cmax * (cmax + 1))));
+        RTR_SMEM(als_solve_inv_kernel, sizeof(double) * (size_t)cmax * (cmax + 1));
     }
     for (int sweep = 0; sweep < p->params.sweeps; ++sweep) {
         for (int n = 0; n < N; ++n) {

@@ -757,10 +757,10 @@ int run_impl(Impl<T>* m, double* err, cudaStream_t s) {
     auto gram = bgram_kernel<T>;
     auto contract = bcontract_kernel<T>;
     auto solve = bsolve_kernel<T>;
-    RTR_CUDA(cudaFuncSetAttribute(contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->ct_smem));
-    RTR_CUDA(cudaFuncSetAttribute(solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->sv_smem));
+    RTR_SMEM(contract, m->ct_smem);
+    RTR_SMEM(solve, m->sv_smem);
     const size_t gsmem = sizeof(T) * 3 * GB * 256;
-    RTR_CUDA(cudaFuncSetAttribute(gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+    RTR_SMEM(gram, gsmem);
     binit_kernel<T><<<m->count, SV_THREADS, 0, s>>>(m->d_tens, N, m->tab);
     RTR_LAUNCH_CHECK("binit_kernel");
     gram<<<(unsigned)std::min(m->n_titems, 4 * m->num_sms), CT_THREADS, gsmem, s>>>(m->d_tens, m->d_titems,

@@ -152,7 +152,7 @@ int gemm(GemmArgs a, cudaStream_t s) {
     a.Np = std::max(16, (a.N + 15) / 16 * 16);
     const size_t stage = A_BYTES + (((size_t)a.Np * 128 + 1023) & ~(size_t)1023);
     const size_t smem = 1024 + 2 * stage + 64;
-    RTR_CUDA(cudaFuncSetAttribute(mlp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(mlp_gemm_kernel, smem);
     mlp_gemm_kernel<<<(unsigned)rtr_ceil_div(a.M, 128), GT, smem, s>>>(a);
     RTR_LAUNCH_CHECK("mlp_gemm_kernel");
     return RTR_OK;
@@ -434,7 +434,7 @@ int rtr_spectrum_features(int N, const int64_t* dims, const int* Kf, const doubl
     }
     const size_t smem = sizeof(double) * (2 * (size_t)kmax * kmax + 2 * ((kmax + 1) / 2 + 1)) +
                         sizeof(int) * 2 * ((kmax + 1) / 2 + 1) + 16;
-    RTR_CUDA(cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(features_kernel, smem);
     features_kernel<<<MODES, 256, smem, (cudaStream_t)stream>>>(a);
     RTR_LAUNCH_CHECK("features_kernel");
     return RTR_OK;

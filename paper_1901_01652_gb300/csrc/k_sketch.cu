@@ -210,7 +210,7 @@ int launch_one(rtr_plan* p, const ContractArgs& a, const Shape& sh, cudaStream_t
     const int KP = sh.NTK * sh.TK;
     size_t smem = sizeof(T) * ((size_t)RC * (sh.rows + 1) + (size_t)RC * KP + (GEN ? 4096 : 0));
     auto kern = contract_kernel<T, TM, TK, GEN>;
-    RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(kern, smem);
     int occ = 0;
     RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
     occ = std::max(1, occ);
@@ -349,7 +349,7 @@ int noalloc_occupancy(NoAllocDevice& d, int ntk, size_t smem, int* out) {
     const int f64 = sizeof(T) == 8;
     if (!d.attr[f64][ti][tk]) {
         const size_t smem_max = sizeof(T) * ((size_t)RC * (256 + 1) + (size_t)RC * 32 * TK + 4096);
-        RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        RTR_SMEM(kern, smem_max);
         d.attr[f64][ti][tk] = 1;
     }
     int& o = d.occ[f64][ti][tk][lg];

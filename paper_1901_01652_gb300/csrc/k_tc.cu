@@ -946,10 +946,10 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     }
     if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     if (a.lm) {
-        RTR_CUDA(cudaFuncSetAttribute(sketch_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RTR_SMEM(sketch_tma_kernel<true>, smem);
         sketch_tma_kernel<true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
     } else {
-        RTR_CUDA(cudaFuncSetAttribute(sketch_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RTR_SMEM(sketch_tma_kernel<false>, smem);
         sketch_tma_kernel<false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
     }
     RTR_LAUNCH_CHECK("sketch_tma_kernel");
@@ -1002,7 +1002,7 @@ int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int
     if ((size_t)(gx * gy) > p->normx_part_elems) return rtr_set_error(RTR_ENOMEM, "norm partials exceed workspace");
     a.partial = p->partial;
     a.normp = norm_out ? p->normx_part : nullptr;
-    RTR_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(sketch_tc_kernel, smem);
     sketch_tc_kernel<<<dim3((unsigned)gx, (unsigned)gy), NTHREADS, smem, s>>>(a);
     RTR_LAUNCH_CHECK("sketch_tc_kernel");
     const int64_t count = I * K;
@@ -1262,7 +1262,7 @@ int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, 
                                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(a.ntiles, p->num_sms));
-    RTR_CUDA(cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(ttm_tc_kernel, smem);
     ttm_tc_kernel<<<(unsigned)gx, TT_NTHREADS, smem, s>>>(tmap, a);
     RTR_LAUNCH_CHECK("ttm_tc_kernel");
     return RTR_OK;

@@ -420,7 +420,7 @@ int jacobi_eig(const T* Cm, int64_t rows, int64_t cols, int left, int m, SvdWs& 
     if (!conv) w.jac_notconv = 1;
     const size_t smem = (size_t)m * (sizeof(double) + sizeof(int));
     if (smem > EIG_SMEM_MAX) return rtr_set_error(RTR_EUNSUPPORTED, "TR-SVD: Gram side %d too large", m);
-    RTR_CUDA(cudaFuncSetAttribute(jac_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(jac_finish_kernel, smem);
     jac_finish_kernel<<<1, 1024, smem, s>>>(w.G, w.V, m, L, w.lam, w.Vs);
     RTR_LAUNCH_CHECK("jac_finish_kernel");
     return RTR_OK;
@@ -450,11 +450,9 @@ int svd_step(const T* Cm, int64_t rows, int64_t cols, double thr, int forced, in
     const size_t sm_bytes = eig32 ? eig_smem_bytes<float>(m) : eig_smem_bytes<double>(m);
     if (sm_bytes <= EIG_SMEM_MAX) {
         if (eig32)
-            RTR_CUDA(cudaFuncSetAttribute(eig_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm_bytes));
+            RTR_SMEM(eig_smem_kernel<float>, sm_bytes);
         else
-            RTR_CUDA(cudaFuncSetAttribute(eig_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm_bytes));
+            RTR_SMEM(eig_smem_kernel<double>, sm_bytes);
         if (eig32) eig_smem_kernel<float><<<1, 1024, sm_bytes, s>>>(w.G, m, w.lam, w.Vs, 60, 1e-13f);
         else eig_smem_kernel<double><<<1, 1024, sm_bytes, s>>>(w.G, m, w.lam, w.Vs, 60, 1e-30);
     } else if (!eig32) {

@@ -257,7 +257,7 @@ int launch_variant(rtr_plan* p, const T* X, int64_t A, int64_t I, int64_t B, con
     else if (B < CT) a.ntiles = rtr_ceil_div(A, CT / B);      // whole a-blocks per tile
     else { a.nbt = rtr_ceil_div(B, CT); a.ntiles = A * a.nbt; }
     auto kern = ttm_kernel<T, TKO, TC>;
-    RTR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RTR_SMEM(kern, smem);
     int occ = 1;
     RTR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ntiles, (int64_t)std::max(occ, 1) * p->num_sms));

@@ -6,7 +6,10 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include "rtr_internal.cuh"
 
 size_t contract_partial_elems(int num_sms, int64_t I, int C);
@@ -152,6 +155,29 @@ void rtr_count_launches(long long delta) { g_launches.fetch_add((unsigned long l
 
 int rtr_cuda_check(cudaError_t e, const char* what) {
     return rtr_set_error(RTR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static std::mutex g_smem_mu;
+static std::map<std::pair<const void*, int>, size_t> g_smem_max;   // (kernel, device) -> dynamic limit
+
+int rtr_smem_limit(const void* kernel, size_t bytes) {
+    int dev = 0;
+    RTR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    auto it = g_smem_max.find({kernel, dev});
+    if (it == g_smem_max.end()) {
+        int optin = 0;
+        RTR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa{};
+        RTR_CUDA(cudaFuncGetAttributes(&fa, kernel));
+        const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        RTR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+        it = g_smem_max.emplace(std::make_pair(kernel, dev), lim).first;
+    }
+    if (bytes > it->second)
+        return rtr_set_error(RTR_EINVAL, "a kernel needs %zu B of dynamic shared memory, the device allows %zu",
+                             bytes, it->second);
+    return RTR_OK;
 }
 
 extern "C" {

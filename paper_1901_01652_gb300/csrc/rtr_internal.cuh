@@ -75,6 +75,16 @@ void rtr_count_launches(long long delta);
 
 static inline int64_t rtr_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Dynamic shared memory of a kernel: the first call for a kernel on a device
+// raises its limit to the device's opt-in maximum (less the kernel's static
+// shared memory); every call checks that `bytes` fits.  The limit is a
+// property of the kernel that is read when a launch runs, also when a CUDA
+// graph replays a recorded launch: setting it to each launch's own size
+// would let a later, smaller launch of the same kernel lower it below what a
+// recorded graph node needs.
+int rtr_smem_limit(const void* kernel, size_t bytes);
+#define RTR_SMEM(kernel, bytes) do { const int st_ = rtr_smem_limit((const void*)(kernel), (size_t)(bytes)); if (st_) return st_; } while (0)
+
 // host copies of the Gaussian quantile table: float64 and bfloat16-rounded
 void rtr_host_tables(double* t64, float* t32);
 
