@@ -702,6 +702,16 @@ struct FusedContractArgs {
     double* partial;            // gridDim.x x (K_n C)
 };
 
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid), so
+// that a thread's gathers are all in flight at once
+__device__ __forceinline__ void fc_cp4(float* dst, const float* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void fc_cp_wait() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <int NT>
 __global__ void __launch_bounds__(FC_THREADS) fused_contract_kernel(const FusedContractArgs a) {
     extern __shared__ __align__(16) float fsm[];
@@ -713,10 +723,14 @@ __global__ void __launch_bounds__(FC_THREADS) fused_contract_kernel(const FusedC
     float* mb = zl + Rl * KL * Rn4;                    // 2 x GB x 256: M of each outer index
     float* Pb = mb + 2 * GB * 256;                     // GB x KL x Kn4: P blocks, i fastest
     float* Sb = Pb + GB * KL * Kn4;                    // GB x KL x C4: slices of S
+    float* zs = Sb + GB * KL * C4;                     // (L - 1) x GB x 256: the outer cores' slices
     const int tid = threadIdx.x;
+    // every global read of the kernel is an asynchronous copy, issued before
+    // the first use: the gathers of a batch wait for one L2 latency, not for
+    // one per element a thread reads
     for (int e = tid; e < Rl * KL * Rn4; e += FC_THREADS) {
         const int g = e % Rn4, hl = e / Rn4;
-        zl[e] = g < Rn ? a.Z[L - 1][(int64_t)hl * Rn + g] : 0.f;
+        fc_cp4(zl + e, g < Rn ? a.Z[L - 1] + (int64_t)hl * Rn + g : a.Z[L - 1], g < Rn);
     }
     const int64_t per = a.nouter / gridDim.x, rem = a.nouter % gridDim.x;
     const int64_t o0 = blockIdx.x * per + min((int64_t)blockIdx.x, rem);
@@ -745,15 +759,26 @@ __global__ void __launch_bounds__(FC_THREADS) fused_contract_kernel(const FusedC
         // P blocks (the inner index fastest in the reads), i fastest in shared memory
         for (int e = tid; e < gb * Kn4 * KL; e += FC_THREADS) {
             const int l = e % KL, r = e / KL, i = r % Kn4, b = r / Kn4;
-            Pb[(b * KL + l) * Kn4 + i] = i < Kn ? a.P[off_s[b] + (int64_t)l * a.st[L - 1] + (int64_t)i * a.stn] : 0.f;
+            fc_cp4(Pb + (b * KL + l) * Kn4 + i,
+                   i < Kn ? a.P + off_s[b] + (int64_t)l * a.st[L - 1] + (int64_t)i * a.stn : a.P, i < Kn);
         }
+        // the outer cores' slices Z[t](j_t) (R[t] x R[t+1]) of every outer index
+        for (int t = 0; t < L - 1; ++t) {
+            const int Rt = a.R[t], Rt1 = a.R[t + 1];
+            for (int e = tid; e < gb * Rt * Rt1; e += FC_THREADS) {
+                const int b = e / (Rt * Rt1), hc = e - b * Rt * Rt1, h = hc / Rt1, c = hc - h * Rt1;
+                fc_cp4(zs + (t * GB + b) * 256 + hc, a.Z[t] + ((int64_t)h * a.K[t] + jo_s[b][t]) * Rt1 + c, true);
+            }
+        }
+        fc_cp_wait();
+        __syncthreads();
         // M(o) = Z[0](j_0) ... Z[L-2](j_{L-2})   (R0 x Rl)
         int mw = 0;
         {
             const int R1 = a.R[1];
             for (int e = tid; e < gb * R0 * R1; e += FC_THREADS) {
-                const int b = e / (R0 * R1), rc = e - b * R0 * R1, r = rc / R1, c = rc - r * R1;
-                mb[b * 256 + rc] = a.Z[0][((int64_t)r * a.K[0] + jo_s[b][0]) * R1 + c];
+                const int b = e / (R0 * R1), rc = e - b * R0 * R1;
+                mb[b * 256 + rc] = zs[b * 256 + rc];
             }
             for (int t = 1; t < L - 1; ++t) {
                 __syncthreads();
@@ -762,9 +787,9 @@ __global__ void __launch_bounds__(FC_THREADS) fused_contract_kernel(const FusedC
                 float* nxt = mb + (mw ^ 1) * GB * 256;
                 for (int e = tid; e < gb * R0 * Rt1; e += FC_THREADS) {
                     const int b = e / (R0 * Rt1), rc = e - b * R0 * Rt1, r = rc / Rt1, c = rc - r * Rt1;
+                    const float* zt = zs + (t * GB + b) * 256 + c;
                     float v = 0.f;
-                    for (int h = 0; h < Rt; ++h)
-                        v = fmaf(cur[b * 256 + r * Rt + h], a.Z[t][((int64_t)h * a.K[t] + jo_s[b][t]) * Rt1 + c], v);
+                    for (int h = 0; h < Rt; ++h) v = fmaf(cur[b * 256 + r * Rt + h], zt[h * Rt1], v);
                     nxt[b * 256 + rc] = v;
                 }
                 mw ^= 1;
@@ -867,7 +892,8 @@ size_t fused_contract_smem(int N, const int64_t* Kd, const int* R, int n, int gb
     const size_t KL = (size_t)Kd[m_last], Rl = (size_t)R[m_last];
     const size_t Rn4 = (size_t)((R[n] + 3) & ~3), Kn4 = (size_t)((Kd[n] + 3) & ~3);
     const size_t C4 = (size_t)((R[(n + 1) % N] * R[n] + 3) & ~3);
-    return sizeof(float) * (Rl * KL * Rn4 + 2 * (size_t)gb * 256 + (size_t)gb * KL * (Kn4 + C4));
+    return sizeof(float) * (Rl * KL * Rn4 + 2 * (size_t)gb * 256 + (size_t)gb * KL * (Kn4 + C4) +
+                            (size_t)(N - 2) * gb * 256);
 }
 
 constexpr size_t FC_SMEM_LIMIT = 200 * 1024;
