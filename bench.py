@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--streams", type=int, default=16, help="worker streams of the batched form")
     ap.add_argument("--batch-count", type=int, default=256, help="tensors of the batched workload (256 = the named workload)")
     ap.add_argument("--no-graph", action="store_true", help="batched form: eager runs, no CUDA graph")
+    ap.add_argument("--batch-inflight", type=int, default=2,
+                    help="batched form: batches in flight (each its own batch object, graph and stream), so that "
+                         "one batch's grouped TR-ALS overlaps the next one's sketches")
     return ap.parse_args()
 
 
@@ -625,23 +628,38 @@ def run_batch(args):
     params = rtr.make_params(cfg["prec"], cfg["seed"], cfg["sweeps"])
     if args.no_graph:
         params.flags = rtr.PARAM_NO_GRAPH
-    b = rtr.rtr_batch_create(shapes, Ks, Rs, params, args.streams)
-    G = [[torch.empty(Rs[t][n] * shapes[t][n] * Rs[t][(n + 1) % N], dtype=torch.float64, device=device)
-          for n in range(N)] for t in range(len(shapes))]
-    rse = torch.empty(len(shapes), dtype=torch.float64, device=device)
+    # batches in flight: step i runs batch object i % nbf on its own stream, so
+    # that one batch's grouped TR-ALS overlaps the next one's sketches
+    nbf = max(1, min(args.batch_inflight, args.steps))
+    batches, Gs, rses = [], [], []
+    for _ in range(nbf):
+        batches.append(rtr.rtr_batch_create(shapes, Ks, Rs, params, args.streams))
+        Gs.append([[torch.empty(Rs[t][n] * shapes[t][n] * Rs[t][(n + 1) % N], dtype=torch.float64, device=device)
+                    for n in range(N)] for t in range(len(shapes))])
+        rses.append(torch.empty(len(shapes), dtype=torch.float64, device=device))
+    b, G, rse = batches[0], Gs[0], rses[0]
     stream = torch.cuda.current_stream(device)
+    bstreams = [torch.cuda.Stream(device) for _ in range(nbf)]
     t_first = time.perf_counter()
     rtr.rtr_batch_run(b, Xs, G, rse, stream)            # eager run, tuning, capture
     torch.cuda.synchronize()
     t_first = time.perf_counter() - t_first
-    for _ in range(max(0, args.warmup - 1)):
-        rtr.rtr_batch_run(b, Xs, G, rse, stream)
+
+    def run_steps(n):
+        for st in bstreams:
+            st.wait_stream(stream)
+        for i in range(n):
+            k = i % nbf
+            rtr.rtr_batch_run(batches[k], Xs, Gs[k], rses[k], bstreams[k])
+        for st in bstreams:
+            stream.wait_stream(st)
+
+    run_steps(max(nbf, args.warmup - 1))                 # every batch object captured and replayed once
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
-            rtr.rtr_batch_run(b, Xs, G, rse, stream)
+        run_steps(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -655,7 +673,8 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD if len(shapes) == 256 else f"first {len(shapes)} tensors of: " + BATCH_WORKLOAD,
                    "tensors": len(shapes), "total_gb": round(xbytes / 1e9, 3),
-                   "streams": args.streams, "graph": not args.no_graph, "prec": cfg["prec"], "l2": "inputs larger than L2 (no flush)",
+                   "streams": args.streams, "graph": not args.no_graph, "batches_in_flight": nbf,
+                   "prec": cfg["prec"], "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas{world}"},
         "rse": {"mean": float(r.mean()), "max": float(r.max())},
         "first_run_s": round(t_first, 3),
@@ -689,7 +708,8 @@ def run_batch(args):
         out["cpu_baseline"] = batch_cpu_baseline(shapes, Ks, Rs, cfg)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    b.close()
+    for bb in batches:
+        bb.close()
 
 
 # ----------------------------------------------------------------------------- other single-tensor workloads
