@@ -657,17 +657,28 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15
                     float4 v[8];
 #pragma unroll
+                    // rows past I were zero-filled by the TMA unit: every row is loaded
                     for (int j = 0; j < 8; ++j) {
                         const int row = (ct >> 4) + 16 * j;
-                        v[j] = row < rows_m ? ld_shared_f4(src + (uint32_t)row * 256u + (uint32_t)(ct & 15) * 16u)
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[j] = ld_shared_f4(src + (uint32_t)row * 256u + (uint32_t)(ct & 15) * 16u);
                         if (want_norm) csum += v[j].x * v[j].x + v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
                     }
                     conv_bar();                        // every piece of this tile is in registers
                     // the swizzle phase (row & 7) is the same for every j
                     const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+                    if (p.fp8) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) piece(v[j], off0 + 2048u * j);
+                        for (int j = 0; j < 8; ++j) piece(v[j], off0 + 2048u * j);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            uint32_t h0, l0, h1, l1;
+                            split2(v[j].x, v[j].y, h0, l0);
+                            split2(v[j].z, v[j].w, h1, l1);
+                            st_shared_v2(hi + off0 + 2048u * j, h0, h1);
+                            st_shared_v2(lo + off0 + 2048u * j, l0, l1);
+                        }
+                    }
                 } else {
                     // kc = 4 Q4 with Q4 a compile-time constant: row/column of a piece
                     // by multiply-shift; zero columns kc .. 16 ksteps - 1 afterwards
