@@ -493,10 +493,14 @@ __device__ __forceinline__ bool conv_bar_and(bool v) {
     return r != 0;
 }
 
-template <bool LM>
+// BF64: BF16 values in 64-wide chunks (every BF16 plan), with the float8
+// and narrow-chunk code compiled out
+template <bool LM, bool BF64>
 __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    const SketchTmaArgs p) {
     extern __shared__ uint8_t smem_raw[];
+    const bool fp8 = BF64 ? false : (p.fp8 != 0);
+    const int kc = BF64 ? 64 : p.kc;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t* sm = smem_raw + pad;
@@ -547,7 +551,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
     const int64_t per_cta = p.nchunks / gridDim.x, rem_cta = p.nchunks % gridDim.x;
     const int64_t c0 = blockIdx.x * per_cta + min((int64_t)blockIdx.x, rem_cta);
     const int64_t nloc = per_cta + ((int64_t)blockIdx.x < rem_cta ? 1 : 0);
-    const int ksteps = (p.kc + 15) >> 4;          // operand columns kc .. 16 ksteps - 1 are written as zeros
+    const int ksteps = (kc + 15) >> 4;          // operand columns kc .. 16 ksteps - 1 are written as zeros
     double nsum = 0.0;
 
     if (warp < TM_CONV_WARPS) {
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                 const uint32_t hi = src, lo = src + TM_TILE / 2;
                 const int rows_m = min(128, rows_valid - 128 * m);
                 auto piece = [&](const float4 v, uint32_t off) {
-                    if (p.fp8) {
+                    if (fp8) {
                         // a 32-value scale block is 8 consecutive pieces of one row,
                         // held by 8 consecutive lanes (kc = 32 or 64)
                         const float mx = group_max(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))), 8);
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     }
                     conv_bar();
                     const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
-                    if (p.fp8) {
+                    if (fp8) {
                         // float8 scale blocks run along a: rows 0-31 and 32-63 of each
                         // column.  This thread's rows of block b are pieces 2b, 2b + 1;
                         // the partner lane (lane ^ 16) holds the next row; the other
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                             st_shared_v2(bx + 8192u + off, l0, l1);
                         }
                     }
-                } else if (p.kc == 64) {
+                } else if (kc == 64) {
                     // piece j of this thread: row (ct >> 4) + 16 j, column group ct & 15
                     float4 v[8];
 #pragma unroll
@@ -666,7 +670,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     conv_bar();                        // every piece of this tile is in registers
                     // the swizzle phase (row & 7) is the same for every j
                     const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
-                    if (p.fp8) {
+                    if (fp8) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) piece(v[j], off0 + 2048u * j);
                     } else {
@@ -706,11 +710,11 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                             for (int pc = ct; pc < 128 * ZP; pc += TM_CONV_THREADS) {
                                 const uint32_t off = sw128_off(pc / ZP, 4 * (Q4 + pc % ZP));
                                 st_shared_v2(hi + off, 0u, 0u);
-                                if (!p.fp8) st_shared_v2(lo + off, 0u, 0u);
+                                if (!fp8) st_shared_v2(lo + off, 0u, 0u);
                             }
                         }
                     };
-                    switch (p.kc >> 2) {
+                    switch (kc >> 2) {
                         case 2: run(std::integral_constant<int, 2>{}); break;
                         case 4: run(std::integral_constant<int, 4>{}); break;
                         case 6: run(std::integral_constant<int, 6>{}); break;
@@ -731,18 +735,18 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
         const int rt = (tid - TM_CONV_THREADS) % TM_RNG_THREADS;
         const int grp = (tid - TM_CONV_THREADS) / TM_RNG_THREADS;
         const int ncall = (p.K + 19) / 20;
-        const int nitems = p.kc * ncall;              // <= 64 * 4 = 2 * TM_RNG_THREADS
+        const int nitems = kc * ncall;              // <= 64 * 4 = 2 * TM_RNG_THREADS
         const int it0 = rt, it1 = rt + TM_RNG_THREADS;
-        const int rr0 = it0 % p.kc, cb0 = it0 / p.kc, rr1 = it1 % p.kc, cb1 = it1 / p.kc;
+        const int rr0 = it0 % kc, cb0 = it0 / kc, rr1 = it1 % kc, cb1 = it1 / kc;
         Ring r(S, grp);
         ChunkPos cp(c0 + grp, (int64_t)TM_RNG_GROUPS, p.nbc);
         for (int64_t t = grp; t < nloc; t += TM_RNG_GROUPS, r.step(TM_RNG_GROUPS), cp.step()) {
             const int s = r.slot;
             const uint32_t u = r.use;
-            const int64_t a = cp.a, b0 = cp.bi * p.kc;
+            const int64_t a = cp.a, b0 = cp.bi * kc;
             // last mode: chunk a covers rows 64 a .. 64 a + 63 of the (A, I) view
             const int64_t r0 = LM ? 64 * a + p.aoff : (a + p.aoff) * p.B + b0;
-            const int len = LM ? (int)min((int64_t)64, p.A - 64 * a) : (int)min((int64_t)p.kc, p.B - b0);
+            const int len = LM ? (int)min((int64_t)64, p.A - 64 * a) : (int)min((int64_t)kc, p.B - b0);
             if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
             const uint32_t bt = sl0 + s * slot_bytes + (uint32_t)MT * TM_TILE;
             for (int item = it0; item < nitems; item += TM_RNG_THREADS) {
@@ -764,12 +768,12 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
         if (lane == 0) {
             Ring r(S);
             ChunkPos cp(c0, 1, p.nbc);
-            const uint32_t box_bytes = (uint32_t)(128 * 4 * p.kc);
+            const uint32_t box_bytes = (uint32_t)(128 * 4 * kc);
             for (int64_t t = 0; t < nloc; ++t, r.step(1), cp.step()) {
                 const int s = r.slot;
                 const uint32_t u = r.use;
                 if (t >= S && !mbar_wait(&empty[s], (u - 1) & 1, abort, p.flags)) break;
-                const int64_t a = cp.a, b0 = cp.bi * p.kc;
+                const int64_t a = cp.a, b0 = cp.bi * kc;
                 // the full boxes are always counted: out-of-range rows (i >= I) and
                 // columns are zero-filled by the TMA unit without memory traffic
                 mbar_arrive_expect_tx(&full[s], box_bytes * (uint32_t)MT);
@@ -808,7 +812,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                         for (int j = 0; j < ksteps; ++j) {
                             const uint64_t bd = sdesc_sw128(bb + 32u * j);
                             mma_bf16(d, sdesc_sw128_mn(ahi + 2048u * j, 16384u), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                            if (!p.fp8) mma_bf16(d, sdesc_sw128_mn(alo + 2048u * j, 16384u), bd, idesc, 1u);
+                            if (!fp8) mma_bf16(d, sdesc_sw128_mn(alo + 2048u * j, 16384u), bd, idesc, 1u);
                         }
                         continue;
                     }
@@ -816,7 +820,7 @@ __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid
                     for (int j = 0; j < ksteps; ++j) {
                         const uint64_t bd = sdesc_sw128(bb + 32u * j);
                         mma_bf16(d, sdesc_sw128(ahi + 32u * j), bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                        if (!p.fp8) mma_bf16(d, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
+                        if (!fp8) mma_bf16(d, sdesc_sw128(alo + 32u * j), bd, idesc, 1u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -957,11 +961,21 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
     }
     if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     if (a.lm) {
-        RTR_SMEM(sketch_tma_kernel<true>, smem);
-        sketch_tma_kernel<true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        if (a.fp8) {
+            RTR_SMEM((sketch_tma_kernel<true, false>), smem);
+            sketch_tma_kernel<true, false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        } else {
+            RTR_SMEM((sketch_tma_kernel<true, true>), smem);
+            sketch_tma_kernel<true, true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        }
     } else {
-        RTR_SMEM(sketch_tma_kernel<false>, smem);
-        sketch_tma_kernel<false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        if (a.fp8 || a.kc != 64) {
+            RTR_SMEM((sketch_tma_kernel<false, false>), smem);
+            sketch_tma_kernel<false, false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        } else {
+            RTR_SMEM((sketch_tma_kernel<false, true>), smem);
+            sketch_tma_kernel<false, true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        }
     }
     RTR_LAUNCH_CHECK("sketch_tma_kernel");
     const int64_t count = I * K;
