@@ -493,14 +493,15 @@ __device__ __forceinline__ bool conv_bar_and(bool v) {
     return r != 0;
 }
 
-// BF64: BF16 values in 64-wide chunks (every BF16 plan), with the float8
-// and narrow-chunk code compiled out
-template <bool LM, bool BF64>
+// VAR: 1 = BF16 values in 64-wide chunks (every BF16 plan), 2 = float8 values
+// in 64-wide chunks, each with the other form's code and the narrow-chunk
+// code compiled out; 0 = any (FP8 in 32-wide chunks)
+template <bool LM, int VAR>
 __global__ void __launch_bounds__(TM_NTHREADS, 1) sketch_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    const SketchTmaArgs p) {
     extern __shared__ uint8_t smem_raw[];
-    const bool fp8 = BF64 ? false : (p.fp8 != 0);
-    const int kc = BF64 ? 64 : p.kc;
+    const bool fp8 = VAR == 1 ? false : VAR == 2 ? true : (p.fp8 != 0);
+    const int kc = VAR != 0 ? 64 : p.kc;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t* sm = smem_raw + pad;
@@ -960,23 +961,19 @@ int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-    if (a.lm) {
-        if (a.fp8) {
-            RTR_SMEM((sketch_tma_kernel<true, false>), smem);
-            sketch_tma_kernel<true, false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
-        } else {
-            RTR_SMEM((sketch_tma_kernel<true, true>), smem);
-            sketch_tma_kernel<true, true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
-        }
-    } else {
-        if (a.fp8 || a.kc != 64) {
-            RTR_SMEM((sketch_tma_kernel<false, false>), smem);
-            sketch_tma_kernel<false, false><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
-        } else {
-            RTR_SMEM((sketch_tma_kernel<false, true>), smem);
-            sketch_tma_kernel<false, true><<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
-        }
-    }
+    // one instantiation per (last mode, value form with 64-wide chunks)
+    auto launch = [&](auto kern) -> int {
+        RTR_SMEM(kern, smem);
+        kern<<<dim3((unsigned)gx, (unsigned)gy), TM_NTHREADS, smem, s>>>(tmap, a);
+        return RTR_OK;
+    };
+    const int var = a.kc != 64 ? 0 : a.fp8 ? 2 : 1;
+    int lst;
+    if (a.lm) lst = var == 1 ? launch(sketch_tma_kernel<true, 1>) : var == 2 ? launch(sketch_tma_kernel<true, 2>)
+                                                                      : launch(sketch_tma_kernel<true, 0>);
+    else lst = var == 1 ? launch(sketch_tma_kernel<false, 1>) : var == 2 ? launch(sketch_tma_kernel<false, 2>)
+                                                                  : launch(sketch_tma_kernel<false, 0>);
+    if (lst) return lst;
     RTR_LAUNCH_CHECK("sketch_tma_kernel");
     const int64_t count = I * K;
     tc_reduce_kernel<<<(unsigned)rtr_ceil_div(count * 32, 256), 256, 0, s>>>(p->partial, (int)gx, count, Y,
