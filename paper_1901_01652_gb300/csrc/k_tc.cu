@@ -1065,13 +1065,14 @@ constexpr int TT_MMA_WARP = TT_CONV_WARPS;
 constexpr int TT_TMA_WARP = TT_CONV_WARPS + 1 + 4;
 constexpr int TT_NTHREADS = (TT_TMA_WARP + 1) * 32;       // converters, MMA issuer, 4 epilogue warps, TMA
 constexpr int TT_CONV_THREADS = TT_CONV_WARPS * 32;
-constexpr int TT_PIECES = 128 * 16 / TT_CONV_THREADS;    // float4 pieces per converter thread per unit
+constexpr int TT_PIECES = 128 * 32 / TT_CONV_THREADS;    // float4 pieces per converter thread per unit
 
 struct TtmTCArgs {
     const double* Q;
     float* out;
     int64_t A;
-    int I, K, N, NKC, S;
+    int I, K, N, NKC, S;          // NKC: 64-wide K atoms of I (Q tiles); a work unit holds two
+    int NKU;                      // work units (128 columns of i) per 128-row tile
     int64_t ntiles;
     int* flags;
 };
@@ -1096,7 +1097,7 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const __grid_con
     uint8_t* sm = smem_raw + pad;
     const uint32_t btile = (uint32_t)p.N * 128u;
     const uint32_t b_bytes = 2u * p.NKC * btile;               // Q hi tiles, then Q lo tiles
-    const uint32_t a_stage = 2u * MTILE_BYTES;                 // one box of 128 x 64 float32 = X hi + X lo
+    const uint32_t a_stage = 4u * MTILE_BYTES;                 // one box of 128 x 128 float32 = 2 x (X hi + X lo)
     const int S = p.S;
     const uint32_t bbase = smem_u32(sm);
     const uint32_t abase = bbase + b_bytes;
@@ -1144,12 +1145,18 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const __grid_con
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int64_t nloc = (blockIdx.x < p.ntiles) ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nunits = nloc * p.NKC;
+    const int64_t nunits = nloc * p.NKU;
 
     if (warp < TT_CONV_WARPS) {
         // ================================================================ converters
+        // a unit is a box of 128 rows x 128 float32 (rows of 512 bytes); it becomes
+        // K atom 0 (columns 0-63: hi at 0, lo at 16 KB) and atom 1 (columns 64-127:
+        // hi at 32 KB, lo at 48 KB).  Thread ct takes column group ct & 31 of rows
+        // (ct >> 5) + 8 q, so the swizzle phase (row & 7) is its warp's for every q.
         const int ct = tid;
-        const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+        const int cg = ct & 31;
+        const uint32_t off0 = (uint32_t)(cg >> 4) * (2u * MTILE_BYTES) +
+                              sw128_off((uint32_t)(ct >> 5), 4u * (uint32_t)(cg & 15));
         Ring rg(S);
         for (int64_t u = 0; u < nunits; ++u, rg.step(1)) {
             const int s = rg.slot;
@@ -1158,15 +1165,15 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const __grid_con
             float4 v[TT_PIECES];
 #pragma unroll
             for (int q = 0; q < TT_PIECES; ++q)
-                v[q] = ld_shared_f4(src + (uint32_t)((ct >> 4) + 16 * q) * 256u + (uint32_t)(ct & 15) * 16u);
+                v[q] = ld_shared_f4(src + (uint32_t)((ct >> 5) + 8 * q) * 512u + (uint32_t)cg * 16u);
             tt_conv_bar();                            // every piece of the box is in registers
 #pragma unroll
             for (int q = 0; q < TT_PIECES; ++q) {
                 uint32_t h0, l0, h1, l1;
                 split2(v[q].x, v[q].y, h0, l0);
                 split2(v[q].z, v[q].w, h1, l1);
-                st_shared_v2(src + off0 + 2048u * q, h0, h1);
-                st_shared_v2(src + MTILE_BYTES + off0 + 2048u * q, l0, l1);
+                st_shared_v2(src + off0 + 1024u * q, h0, h1);
+                st_shared_v2(src + MTILE_BYTES + off0 + 1024u * q, l0, l1);
             }
             fence_proxy_async();
             __syncwarp();
@@ -1182,20 +1189,24 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const __grid_con
             if (j >= 2 && !mbar_wait(&acce[buf], (uint32_t)(((j >> 1) - 1) & 1), abort, p.flags)) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(buf * p.N);
-            for (int c = 0; c < p.NKC; ++c, rg.step(1)) {
+            for (int cu = 0; cu < p.NKU; ++cu, rg.step(1)) {
                 const int s = rg.slot;
                 if (!mbar_wait(&conv[s], rg.use & 1, abort, p.flags)) { ok = false; break; }
                 tc_fence_after();
                 if (lane == 0) {
-                    const uint32_t ahi = abase + s * a_stage, alo = ahi + MTILE_BYTES;
-                    const uint32_t bhi = bbase + c * btile, blo = bbase + (p.NKC + c) * btile;
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = 2 * cu + h;             // K atom of I
+                        if (c >= p.NKC) break;
+                        const uint32_t ahi = abase + s * a_stage + (uint32_t)h * 2u * MTILE_BYTES, alo = ahi + MTILE_BYTES;
+                        const uint32_t bhi = bbase + c * btile, blo = bbase + (p.NKC + c) * btile;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t dah = sdesc_sw128(ahi + 32u * kk), dal = sdesc_sw128(alo + 32u * kk);
-                        const uint64_t dbh = sdesc_sw128(bhi + 32u * kk), dbl = sdesc_sw128(blo + 32u * kk);
-                        mma_bf16(d, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_bf16(d, dal, dbh, idesc, 1u);
-                        mma_bf16(d, dah, dbl, idesc, 1u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t dah = sdesc_sw128(ahi + 32u * kk), dal = sdesc_sw128(alo + 32u * kk);
+                            const uint64_t dbh = sdesc_sw128(bhi + 32u * kk), dbl = sdesc_sw128(blo + 32u * kk);
+                            mma_bf16(d, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(d, dal, dbh, idesc, 1u);
+                            mma_bf16(d, dah, dbl, idesc, 1u);
+                        }
                     }
                     mma_commit(&empty[s]);
                 }
@@ -1238,8 +1249,8 @@ __global__ void __launch_bounds__(TT_NTHREADS, 1) ttm_tc_kernel(const __grid_con
                 const int64_t a0 = (blockIdx.x + j * gridDim.x) * 128;
                 // rows a >= A and columns i >= I are zero-filled without memory traffic
                 mbar_arrive_expect_tx(&full[s], (uint32_t)a_stage);
-                tma_load_2d(abase + s * a_stage, &tmap, c * 64, (int)a0, &full[s]);
-                if (++c == p.NKC) { c = 0; ++j; }
+                tma_load_2d(abase + s * a_stage, &tmap, c * 128, (int)a0, &full[s]);
+                if (++c == p.NKU) { c = 0; ++j; }
             }
         }
         __syncwarp();
@@ -1264,19 +1275,20 @@ int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, 
     a.Q = Q; a.out = out; a.A = A; a.I = (int)I; a.K = K;
     a.N = (K <= 32) ? 32 : 64;
     a.NKC = (int)rtr_ceil_div(I, 64);
+    a.NKU = (int)rtr_ceil_div(I, 128);
     a.ntiles = rtr_ceil_div(A, 128);
     a.flags = p->flags;
     const size_t bq = 2 * (size_t)a.NKC * a.N * 128;
     const size_t fixed = 1024 + 256;
-    int S = (int)((SMEM_LIMIT - fixed - bq) / (2 * MTILE_BYTES));
+    int S = (int)((SMEM_LIMIT - fixed - bq) / (4 * MTILE_BYTES));
     S = std::min(S, 6);
     if (S < 2) return launch_ttm(p, 0, X, A, I, B, Q, K, out, s);
     a.S = S;
-    const size_t smem = fixed + bq + (size_t)S * 2 * MTILE_BYTES;
+    const size_t smem = fixed + bq + (size_t)S * 4 * MTILE_BYTES;
     CUtensorMap tmap;
     const cuuint64_t gdim[2] = {(cuuint64_t)I, (cuuint64_t)A};
     const cuuint64_t gstride[1] = {(cuuint64_t)I * 4};
-    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t box[2] = {128, 128};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), gdim,
                                              gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

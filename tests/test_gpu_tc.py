@@ -110,7 +110,10 @@ def test_bf16_end_to_end_vs_oracle():
 
 @pytest.mark.parametrize("dims,K", [((40, 48, 44, 52), (10, 10, 10, 10)),   # last mode first, vector loads
                                     ((7, 9, 11, 203), (3, 4, 5, 60)),        # I = 203 (scalar path), N = 64
-                                    ((30, 17, 256), (5, 6, 25))])            # I = 256: four full chunks
+                                    ((30, 17, 256), (5, 6, 25)),             # I = 256: two full 128-wide units
+                                    ((12, 10, 132), (5, 4, 20)),             # I = 132: three K atoms, the last unit half empty
+                                    ((9, 8, 5, 100), (4, 4, 3, 30)),         # I = 100: one unit, two atoms
+                                    ((16, 12, 200), (6, 5, 40))])            # I = 200, K = 40 (N = 64: two slots)
 def test_bf16_chain_vs_oracle(dims, K):
     """rtr_project on a BF16 plan (tensor-core first product) from the oracle's Y."""
     X32 = np.random.default_rng(23).standard_normal(dims).astype(np.float32)
