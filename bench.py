@@ -794,15 +794,53 @@ def run_single(args):
     eng = RTRD(spec["dims"], spec["K"], spec["R"], spec["prec"], spec["seed"], spec["sweeps"],
                spec["eps"] or 1e-2, chain_order=spec.get("chain_order"), device=device)
     stream = torch.cuda.current_stream(device)
-    for _ in range(args.warmup):
-        single_step(eng, X, spec, stream)
+    # tensors in flight, one plan and stream each: tensor i + depth's passes
+    # over X are enqueued before tensor i's decomposition, whose latency-bound
+    # kernels then run beside them (TR-SVD reads its chosen ranks back on the
+    # host, so the next tensor's work has to be in the queues before it)
+    nf = max(1, min(args.inflight, max(2, args.steps - 1)))
+    engs = [eng] + [RTRD(spec["dims"], spec["K"], spec["R"], spec["prec"], spec["seed"], spec["sweeps"],
+                         spec["eps"] or 1e-2, chain_order=spec.get("chain_order"), device=device)
+                    for _ in range(nf - 1)]
+    streams = [torch.cuda.Stream(device) for _ in engs]
+
+    def front(i):
+        k = i % nf
+        with torch.cuda.stream(streams[k]):
+            engs[k].sketch(X, streams[k])
+            engs[k].project(X, streams[k])
+
+    def back(i):
+        k = i % nf
+        e, st = engs[k], streams[k]
+        with torch.cuda.stream(st):
+            if spec["method"] == "als":
+                e.als(None, st)
+            else:
+                e.svd(spec["eps"], None, st)
+            e.backproject(st)
+            e.compute_rse(st)
+
+    def run_steps(n):
+        depth = max(1, nf - 1)
+        for st in streams:
+            st.wait_stream(stream)
+        for i in range(min(depth, n)):
+            front(i)
+        for i in range(n):
+            if i + depth < n:
+                front(i + depth)
+            back(i)
+        for st in streams:
+            stream.wait_stream(st)
+
+    run_steps(max(args.warmup, nf))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = rtr.rtr_kernel_launches()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
-            single_step(eng, X, spec, stream)
+        run_steps(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
     launches = rtr.rtr_kernel_launches() - l0
@@ -829,7 +867,7 @@ def run_single(args):
                    "prec": spec["prec"], "method": spec["method"], "l2": "inputs larger than L2 (no flush)"
                    if xbytes > 129e6 else "input smaller than L2 (resident between steps)",
                    "parallelism": f"replicas{world}"},
-        "rse": float(eng.rse.cpu()[0]), "ranks": list(eng.ranks),
+        "rse": float(eng.rse.cpu()[0]), "ranks": list(eng.ranks), "inflight": nf,
         "gpu_launches": int(launches), "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
