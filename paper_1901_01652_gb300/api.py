@@ -12,11 +12,13 @@ from . import rtr
 
 class RTRD:
     def __init__(self, dims, K, R, prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None,
-                 device="cuda", power=0, sequential=False):
+                 device="cuda", power=0, sequential=False, pair=False):
         """power: power iterations per sketch (the remark after Algorithm 1);
         sequential: the sequential projection (rtr_project_sequential) in place
-        of steps 3-8."""
-        self.params = rtr.make_params(prec, seed, sweeps, tol, chain_order, power)
+        of steps 3-8; pair: a BF16 plan sketches its last two modes from the
+        same tiles of X (RTR_PARAM_PAIR)."""
+        self.params = rtr.make_params(prec, seed, sweeps, tol, chain_order, power,
+                                      flags=rtr.PARAM_PAIR if pair else 0)
         self.sequential = bool(sequential)
         with torch.cuda.device(device):
             self.plan = rtr.rtr_plan_create(dims, K, R, self.params)

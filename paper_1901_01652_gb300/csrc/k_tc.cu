@@ -900,7 +900,467 @@ int sketch_geometry(int64_t I, int K, int* MT, int* N, int* S, size_t* smem) {
     return 1;
 }
 
+// ---- the last two modes in one read of X (BF16) ------------------------------
+// Algorithm 1 step 5 for modes N-2 and N-1 together, X viewed as (A, I, J)
+// with I = I_{N-2}, J = I_{N-1} and a the flat index of the leading modes:
+//     Y_{N-2}[i, k] = sum_{a, j} X[a, i, j] Omega_{N-2}[a J + j, k]
+//     Y_{N-1}[j, k] = sum_{a, i} X[a, i, j] Omega_{N-1}[a I + i, k]
+// Both sums run over the same elements, so one tile of X in shared memory
+// feeds both products and X is read once for the two modes.  A chunk is
+// (a, jt, it): 128 rows of i (tile it) x 128 consecutive j (tile jt, the last
+// one ragged), and a CTA walks a contiguous range of chunks in that order (it
+// fastest).  A chunk arrives by TMA as two boxes of 128 i x 64 j float32 (32 KB
+// each) and is converted in place into bf16 hi/lo tiles exactly as in
+// sketch_tma_kernel (rows i, 64 j in each 128-byte SW128 row).  Read with a
+// K-major descriptor the tiles are the A operand of mode N-2 (M = i, K = j, two
+// K atoms); read with an MN-major descriptor the same bytes are the A operand
+// of mode N-1 (M = j in two 64-wide halves 32 KB apart, K = i in eight steps
+// of 16 rows).  The Omega tiles are drawn once per use group: the mode N-2
+// tile of (a, jt) serves the consecutive chunks it = 0 .. nit - 1, and the
+// mode N-1 tiles of a (all of i) serve every chunk of that a; each kind has a
+// ring of two groups, released by the MMA of the group's last chunk.  So per
+// element of X as many Omega rows are drawn as by the two one-mode passes.
+// The quantile table is read through the L1 cache.  TMEM holds one mode N-2
+// accumulator per i tile and one mode N-1 accumulator per j tile.
+//   warps 0-7    converters; then warps 0-3 drain mode N-2, warps 4-7 mode N-1
+//   warps 8-13   Omega generators (both modes)
+//   warp 14      TMA producer (one lane)
+//   warp 15      MMA issuer (one lane)
+constexpr int PR_CONV_WARPS = TM_CONV_WARPS;
+constexpr int PR_RNG_WARPS = 6;
+constexpr int PR_TMA_WARP = PR_CONV_WARPS + PR_RNG_WARPS;
+constexpr int PR_MMA_WARP = PR_TMA_WARP + 1;
+constexpr int PR_NTHREADS = (PR_MMA_WARP + 1) * 32;
+constexpr int PR_RNG_THREADS = PR_RNG_WARPS * 32;
+constexpr uint32_t PR_XSLOT = 2 * TM_TILE;       // two boxes of 128 i x 64 j float32
+constexpr int PR_MAX_XS = 3;                     // X slots
+
+struct SketchPairArgs {
+    int64_t A;
+    int I, J, K2, K3, N2, N3, S, nit, njt;
+    int64_t nchunks;              // A * njt * nit
+    uint64_t seed;
+    int mode2, mode3;             // N - 2, N - 1
+    const uint16_t* tab;          // bfloat16 quantile table (global)
+    double* part2;                // [gridDim.x][I][K2]
+    double* part3;                // [gridDim.x][J][K3]
+    double* normp;                // [gridDim.x] or null
+    int* flags;
+};
+
+// 64-wide K atoms of a chunk that hold any j < J (1 or 2)
+__device__ __forceinline__ int pair_atoms(int J, int jt) { return min(2, (J - 128 * jt + 63) >> 6); }
+
+// (a, jt, it) of chunk c = (a njt + jt) nit + it, stepped without divisions
+struct PairPos {
+    int64_t a;
+    int jt, it;
+    __device__ PairPos(int64_t c, int nit, int njt) {
+        it = (int)(c % nit);
+        const int64_t q = c / nit;
+        jt = (int)(q % njt);
+        a = q / njt;
+    }
+    __device__ void step(int nit, int njt) {
+        if (++it == nit) {
+            it = 0;
+            if (++jt == njt) { jt = 0; ++a; }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(PR_NTHREADS, 1) sketch_pair_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                     const SketchPairArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    uint8_t* sm = smem_raw + pad;
+    const int S = p.S, nit = p.nit, njt = p.njt;
+    const uint32_t b2_tile = 2u * (uint32_t)p.N2 * 128u;            // 128 rows of reduction, two K atoms
+    const uint32_t b3_tile = 2u * (uint32_t)p.N3 * 128u;
+    const uint32_t b3_group = (uint32_t)nit * b3_tile;
+    const uint32_t xs0 = smem_u32(sm);
+    const uint32_t b2s0 = xs0 + (uint32_t)S * PR_XSLOT;             // ring of 2 mode N-2 tiles
+    const uint32_t b3s0 = b2s0 + 2u * b2_tile;                      // ring of 2 groups of nit mode N-1 tiles
+    const uint32_t total = (uint32_t)S * PR_XSLOT + 2u * b2_tile + 2u * b3_group;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + total);
+    uint64_t* full = bars;                 // X boxes landed (transaction bytes)
+    uint64_t* conv = bars + S;             // hi/lo tiles written (8 converter warps)
+    uint64_t* empty = bars + 2 * S;        // MMAs reading the X slot done
+    uint64_t* full2 = bars + 3 * S;        // mode N-2 Omega tile written (6 generator warps)
+    uint64_t* empty2 = full2 + 2;          // MMAs of the tile's last chunk done
+    uint64_t* full3 = full2 + 4;           // mode N-1 Omega group written
+    uint64_t* empty3 = full2 + 6;
+    uint64_t* accf = full2 + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    double* nred = reinterpret_cast<double*>(accf + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)(nit * p.N2 + njt * p.N3)) ncols <<= 1;
+
+    // zero every slot once: Omega columns k >= K are never written
+    for (uint32_t off = tid * 16u; off < total; off += PR_NTHREADS * 16u)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(xs0 + off), "r"(0) : "memory");
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], PR_CONV_WARPS);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full2[s], PR_RNG_WARPS);
+            mbar_init(&empty2[s], 1);
+            mbar_init(&full3[s], PR_RNG_WARPS);
+            mbar_init(&empty3[s], 1);
+        }
+        mbar_init(accf, 1);
+        *abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == PR_MMA_WARP) tmem_alloc(tmem_slot, ncols);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t per_cta = p.nchunks / gridDim.x, rem_cta = p.nchunks % gridDim.x;
+    const int64_t c0 = blockIdx.x * per_cta + min((int64_t)blockIdx.x, rem_cta);
+    const int64_t nloc = per_cta + ((int64_t)blockIdx.x < rem_cta ? 1 : 0);
+    double nsum = 0.0;
+
+    if (warp < PR_CONV_WARPS) {
+        // ================================================================ converters
+        const int ct = tid;
+        const bool want_norm = p.normp != nullptr;
+        Ring r(S);
+        PairPos pos(c0, nit, njt);
+        for (int64_t t = 0; t < nloc; ++t, r.step(1), pos.step(nit, njt)) {
+            const int s = r.slot;
+            if (!conv_bar_and(mbar_wait(&full[s], r.use & 1, abort, p.flags))) break;
+            const int nat = pair_atoms(p.J, pos.jt);
+            float csum = 0.f;
+            for (int h = 0; h < nat; ++h) {
+                // box h: 128 rows of i x 64 j; piece j of this thread: row
+                // (ct >> 4) + 16 j, column group ct & 15; rows past I and
+                // columns past J were zero-filled by the TMA unit
+                const uint32_t src = xs0 + s * PR_XSLOT + h * TM_TILE;
+                float4 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int row = (ct >> 4) + 16 * j;
+                    v[j] = ld_shared_f4(src + (uint32_t)row * 256u + (uint32_t)(ct & 15) * 16u);
+                    if (want_norm) csum += v[j].x * v[j].x + v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
+                }
+                conv_bar();                        // every piece of this box is in registers
+                const uint32_t off0 = sw128_off((uint32_t)(ct >> 4), 4u * (uint32_t)(ct & 15));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint32_t h0, l0, h1, l1;
+                    split2(v[j].x, v[j].y, h0, l0);
+                    split2(v[j].z, v[j].w, h1, l1);
+                    st_shared_v2(src + off0 + 2048u * j, h0, h1);
+                    st_shared_v2(src + TM_TILE / 2 + off0 + 2048u * j, l0, l1);
+                }
+            }
+            nsum += (double)csum;
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[s]);
+        }
+    } else if (warp < PR_TMA_WARP) {
+        // ================================================================ Omega generators
+        // A tile holds `nrows` reduction rows (128 per tile, tiles consecutive)
+        // of Omega_mode from row `row0` on; rows at or past `lim` are zero.
+        // Items: (rows 2 rp, 2 rp + 1, Philox call cb).  A thread draws both
+        // rows, looks up all 40 table entries before its first store (the
+        // stores are ordered asm, so a lookup placed between them would wait
+        // out its full latency each time) and writes the pairs as 32-bit
+        // words (adjacent rows are adjacent bf16).
+        const int gt = tid - PR_CONV_WARPS * 32;
+        auto draw = [&](uint32_t base, int nrows, int Nc, int K, int mode, uint64_t row0, int lim) {
+            const int npair = nrows >> 1, items = npair * ((K + 19) / 20);
+            for (int item = gt; item < items; item += PR_RNG_THREADS) {
+                const int rp = item % npair, cb = item / npair;
+                const int rr = 2 * rp;
+                const uint32_t bt = base + (uint32_t)(rr >> 6) * (uint32_t)Nc * 128u;   // tiles, then atoms, consecutive
+                uint64_t w0[4] = {0, 0, 0, 0}, w1[4] = {0, 0, 0, 0};
+                if (rr < lim) rtr::omega_words(p.seed, mode, row0 + rr, (uint64_t)cb, w0);
+                if (rr + 1 < lim) rtr::omega_words(p.seed, mode, row0 + rr + 1, (uint64_t)cb, w1);
+                uint32_t v[20];
+#pragma unroll
+                for (int tt = 0; tt < 20; ++tt) {
+                    const uint32_t e0 = rr < lim ? (uint32_t)__ldg(p.tab + rtr::omega_field(w0, tt)) : 0u;
+                    const uint32_t e1 = rr + 1 < lim ? (uint32_t)__ldg(p.tab + rtr::omega_field(w1, tt)) : 0u;
+                    v[tt] = e0 | (e1 << 16);
+                }
+#pragma unroll
+                for (int tt = 0; tt < 20; ++tt) {
+                    const int k = cb * 20 + tt;
+                    if (k < K) st_shared_u32(bt + sw128_off(k, rr & 63), v[tt]);
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+        };
+        PairPos pos(c0, nit, njt);
+        int64_t g2 = -1, g3 = -1;
+        for (int64_t t = 0; t < nloc; ++t, pos.step(nit, njt)) {
+            if (t == 0 || (pos.jt == 0 && pos.it == 0)) {
+                // a new a: the mode N-1 tiles of all of i
+                ++g3;
+                const int s3 = (int)(g3 & 1);
+                if (g3 >= 2 && !mbar_wait(&empty3[s3], (uint32_t)((g3 >> 1) - 1) & 1, abort, p.flags)) break;
+                draw(b3s0 + s3 * b3_group, 128 * nit, p.N3, p.K3, p.mode3, (uint64_t)(pos.a * p.I), p.I);
+                if (lane == 0) mbar_arrive(&full3[s3]);
+            }
+            if (t == 0 || pos.it == 0) {
+                // a new (a, jt): the mode N-2 tile of 128 j
+                ++g2;
+                const int s2 = (int)(g2 & 1);
+                if (g2 >= 2 && !mbar_wait(&empty2[s2], (uint32_t)((g2 >> 1) - 1) & 1, abort, p.flags)) break;
+                draw(b2s0 + s2 * b2_tile, 128, p.N2, p.K2, p.mode2, (uint64_t)(pos.a * p.J + 128 * pos.jt),
+                     p.J - 128 * pos.jt);
+                if (lane == 0) mbar_arrive(&full2[s2]);
+            }
+        }
+    } else if (warp == PR_TMA_WARP) {
+        // ================================================================ TMA producer
+        if (lane == 0) {
+            Ring r(S);
+            PairPos pos(c0, nit, njt);
+            for (int64_t t = 0; t < nloc; ++t, r.step(1), pos.step(nit, njt)) {
+                const int s = r.slot;
+                if (t >= S && !mbar_wait(&empty[s], (r.use - 1) & 1, abort, p.flags)) break;
+                const int nat = pair_atoms(p.J, pos.jt);
+                // a box past J is not loaded (its tiles are neither converted
+                // nor read by the mode N-2 product)
+                mbar_arrive_expect_tx(&full[s], (uint32_t)nat * TM_TILE);
+                for (int h = 0; h < nat; ++h)
+                    tma_load_3d(xs0 + s * PR_XSLOT + h * TM_TILE, &tmap, 128 * pos.jt + 64 * h, 128 * pos.it,
+                                (int)pos.a, &full[s]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ================================================================ MMA issuer
+        const uint32_t id2 = idesc_bf16_f32(128, p.N2);
+        const uint32_t id3 = idesc_bf16_f32(128, p.N3) | IDESC_A_MN_MAJOR;
+        Ring r(S);
+        PairPos pos(c0, nit, njt);
+        int64_t g2 = -1, g3 = -1;
+        uint64_t init = 0;           // bit it: mode N-2 tile it written; bit 32 + jt: mode N-1 tile jt
+        for (int64_t t = 0; t < nloc; ++t, r.step(1), pos.step(nit, njt)) {
+            const int s = r.slot;
+            const bool new3 = t == 0 || (pos.jt == 0 && pos.it == 0), new2 = t == 0 || pos.it == 0;
+            const bool last = t == nloc - 1;
+            const bool last2 = last || pos.it == nit - 1, last3 = last || (pos.jt == njt - 1 && pos.it == nit - 1);
+            if (new3) ++g3;
+            if (new2) ++g2;
+            const int s2 = (int)(g2 & 1), s3 = (int)(g3 & 1);
+            if (!mbar_wait(&conv[s], r.use & 1, abort, p.flags)) break;
+            if (new3 && !mbar_wait(&full3[s3], (uint32_t)(g3 >> 1) & 1, abort, p.flags)) break;
+            if (new2 && !mbar_wait(&full2[s2], (uint32_t)(g2 >> 1) & 1, abort, p.flags)) break;
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t xa = xs0 + s * PR_XSLOT;
+                const uint32_t b2 = b2s0 + s2 * b2_tile;
+                const uint32_t b3 = b3s0 + s3 * b3_group + (uint32_t)pos.it * b3_tile;
+                const int nat = pair_atoms(p.J, pos.jt);
+                // mode N-2: D2[it][i, k] += A[i, j] B2[j, k], K atom h = j 64 h .. 64 h + 63
+                const uint32_t d2 = tmem + (uint32_t)(pos.it * p.N2);
+                const uint64_t bit2 = 1ull << pos.it;
+                for (int h = 0; h < nat; ++h) {
+                    const uint32_t ahi = xa + (uint32_t)h * TM_TILE, alo = ahi + TM_TILE / 2;
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t bd = sdesc_sw128(b2 + (uint32_t)h * (uint32_t)p.N2 * 128u + 32u * ks);
+                        mma_bf16(d2, sdesc_sw128(ahi + 32u * ks), bd, id2, (init & bit2) ? 1u : 0u);
+                        init |= bit2;
+                        mma_bf16(d2, sdesc_sw128(alo + 32u * ks), bd, id2, 1u);
+                    }
+                }
+                // mode N-1: D3[jt][j, k] += A[j, i] B3[i, k] on the same tiles read
+                // MN-major: 8-row groups of i 1024 B apart, the two 64-wide halves
+                // of j one box (32 KB) apart; K step kk = rows 16 kk .. 16 kk + 15
+                const uint32_t d3 = tmem + (uint32_t)(nit * p.N2 + pos.jt * p.N3);
+                const uint64_t bit3 = 1ull << (32 + pos.jt);
+                for (int kk = 0; kk < 8; ++kk) {
+                    const uint64_t bd = sdesc_sw128(b3 + (uint32_t)(kk >> 2) * (uint32_t)p.N3 * 128u + 32u * (kk & 3));
+                    mma_bf16(d3, sdesc_sw128_mn(xa + 2048u * kk, TM_TILE), bd, id3, (init & bit3) ? 1u : 0u);
+                    init |= bit3;
+                    mma_bf16(d3, sdesc_sw128_mn(xa + TM_TILE / 2 + 2048u * kk, TM_TILE), bd, id3, 1u);
+                }
+                mma_commit(&empty[s]);
+                if (last2) mma_commit(&empty2[s2]);
+                if (last3) mma_commit(&empty3[s3]);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) mma_commit(accf);
+        __syncwarp();
+    }
+
+    // ==================================================================== epilogue
+    if (warp < PR_CONV_WARPS) {
+        const bool have = nloc > 0;
+        bool ok = true;
+        if (have) {
+            ok = mbar_wait(accf, 0, abort, p.flags);
+            tc_fence_after();
+        }
+        const int q = warp & 3;
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        if (warp < 4) {
+            // tile it was written iff the CTA's chunks c0 .. c0 + nloc - 1 include one with it
+            const int it0 = (int)(c0 % nit);
+            for (int it = 0; it < nit; ++it) {
+                const bool touched = have && ok && (nloc >= nit || (it - it0 + nit) % nit < nloc);
+                const int row = 128 * it + 32 * q + lane;
+                for (int cc = 0; cc < p.N2; cc += 32) {
+                    float v[32];
+                    if (touched) {
+                        tmem_ld32(tmem + lanes + (uint32_t)(it * p.N2 + cc), v);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) v[k] = 0.f;
+                    }
+                    if (row < p.I) {
+                        double* dst = p.part2 + ((int64_t)blockIdx.x * p.I + row) * p.K2;
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            if (cc + k < p.K2) dst[cc + k] = (double)v[k];
+                    }
+                }
+            }
+        } else {
+            // the chunks' (a, jt) groups q0 .. q1 are consecutive; tile jt was
+            // written iff one of them has jt
+            const int64_t q0 = c0 / nit, q1 = have ? (c0 + nloc - 1) / nit : q0 - 1;
+            const int jt0 = (int)(q0 % njt);
+            for (int jt = 0; jt < njt; ++jt) {
+                const bool touched = have && ok && (q1 - q0 + 1 >= njt || (jt - jt0 + njt) % njt <= q1 - q0);
+                const int j = 128 * jt + 32 * q + lane;
+                for (int cc = 0; cc < p.N3; cc += 32) {
+                    float v[32];
+                    if (touched) {
+                        tmem_ld32(tmem + lanes + (uint32_t)(nit * p.N2 + jt * p.N3 + cc), v);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) v[k] = 0.f;
+                    }
+                    if (j < p.J) {
+                        double* dst = p.part3 + ((int64_t)blockIdx.x * p.J + j) * p.K3;
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            if (cc + k < p.K3) dst[cc + k] = (double)v[k];
+                    }
+                }
+            }
+        }
+    }
+    if (warp < PR_CONV_WARPS && p.normp) {
+        nsum = rtr::warp_sum(nsum);
+        if (lane == 0) nred[warp] = nsum;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (p.normp && tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < PR_CONV_WARPS; ++w) s += nred[w];
+        p.normp[blockIdx.x] = s;
+    }
+    if (warp == PR_MMA_WARP) tmem_dealloc(tmem, ncols);
+}
+
+// Launch geometry of sketch_pair_kernel for plan p, or 0 when the plan does
+// not take the two-mode pass (not BF16 or no RTR_PARAM_PAIR, one of the two modes
+// not projected, J % 4 != 0, the accumulators, Omega rings or partial sums
+// do not fit).
+struct PairGeom {
+    int64_t A, I, J;
+    int N2, N3, S, nit, njt, gx;
+    size_t smem;
+};
+
+int pair_geometry(const rtr_plan* p, PairGeom* g) {
+    const int N = p->N;
+    if (N < 3 || p->params.prec != RTR_BF16 || !(p->params.flags & RTR_PARAM_PAIR)) return 0;
+    if (!p->proj[N - 2] || !p->proj[N - 1]) return 0;
+    g->I = p->dims[N - 2];
+    g->J = p->dims[N - 1];
+    g->A = p->numel / (g->I * g->J);
+    if (g->J % 4 != 0 || g->A >= ((int64_t)1 << 31) || g->I >= ((int64_t)1 << 30)) return 0;
+    g->N2 = p->K[N - 2] <= 32 ? 32 : 64;
+    g->N3 = p->K[N - 1] <= 32 ? 32 : 64;
+    g->nit = (int)rtr_ceil_div(g->I, 128);
+    g->njt = (int)rtr_ceil_div(g->J, 128);
+    if (g->nit > 32 || g->njt > 32 || g->nit * g->N2 + g->njt * g->N3 > 512) return 0;
+    const size_t omega = 2 * 256 * (size_t)g->N2 + 2 * (size_t)g->nit * 256 * g->N3;   // both rings
+    const size_t fixed = (3 * PR_MAX_XS + 9 + 1) * 8 + 64 + 1024;                    // barriers, scalars, alignment
+    if (SMEM_LIMIT < fixed + omega + 2 * (size_t)PR_XSLOT) return 0;
+    g->S = (int)std::min<size_t>(PR_MAX_XS, (SMEM_LIMIT - fixed - omega) / PR_XSLOT);
+    g->smem = fixed + (size_t)g->S * PR_XSLOT + omega;
+    const int64_t nchunks = g->A * g->njt * g->nit;
+    g->gx = (int)std::min<int64_t>(p->num_sms, nchunks);
+    const size_t need = (size_t)g->gx * (g->I * p->K[N - 2] + g->J * p->K[N - 1]);
+    if (need > p->partial_elems || (size_t)g->gx > p->normx_part_elems) return 0;
+    return 1;
+}
+
 }  // namespace
+
+size_t pair_partial_elems(int num_sms, int64_t I, int K2, int64_t J, int K3) {
+    return (size_t)num_sms * ((size_t)I * K2 + (size_t)J * K3);
+}
+
+int sketch_passes(const rtr_plan* p) {
+    PairGeom g;
+    int n = 0;
+    for (int m = 0; m < p->N; ++m) n += p->proj[m] ? 1 : 0;
+    return pair_geometry(p, &g) ? n - 1 : n;
+}
+
+// Modes N-2 and N-1 of the BF16 sketch in one pass over X; *done = 0 (and
+// nothing launched) when the plan does not take that pass.
+int launch_sketch_pair(rtr_plan* p, const float* X, double* Y2, double* Y3, double* norm_out, cudaStream_t s,
+                       int* done) {
+    *done = 0;
+    PairGeom g;
+    if ((reinterpret_cast<uintptr_t>(X) & 15) != 0 || !tensor_map_encoder() || !pair_geometry(p, &g)) return RTR_OK;
+    const int N = p->N;
+    SketchPairArgs a{};
+    a.A = g.A; a.I = (int)g.I; a.J = (int)g.J;
+    a.K2 = p->K[N - 2]; a.K3 = p->K[N - 1]; a.N2 = g.N2; a.N3 = g.N3; a.S = g.S; a.nit = g.nit; a.njt = g.njt;
+    a.nchunks = g.A * g.njt * g.nit;
+    a.seed = p->params.seed; a.mode2 = N - 2; a.mode3 = N - 1;
+    a.tab = p->tab_bf16; a.flags = p->flags;
+    a.part2 = p->partial;
+    a.part3 = p->partial + (size_t)g.gx * g.I * a.K2;
+    a.normp = norm_out ? p->normx_part : nullptr;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[3] = {(cuuint64_t)g.J, (cuuint64_t)g.I, (cuuint64_t)g.A};
+    const cuuint64_t gstride[2] = {(cuuint64_t)g.J * 4, (cuuint64_t)g.I * g.J * 4};
+    const cuuint32_t box[3] = {64, 128, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult cr = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), gdim,
+                                             gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return rtr_set_error(RTR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    RTR_SMEM(sketch_pair_kernel, g.smem);
+    sketch_pair_kernel<<<(unsigned)g.gx, PR_NTHREADS, g.smem, s>>>(tmap, a);
+    RTR_LAUNCH_CHECK("sketch_pair_kernel");
+    const int64_t c2 = g.I * a.K2, c3 = g.J * a.K3;
+    tc_reduce_kernel<<<(unsigned)rtr_ceil_div(c2 * 32, 256), 256, 0, s>>>(a.part2, g.gx, c2, Y2, p->normx_part, g.gx,
+                                                                        norm_out, p->flags);
+    RTR_LAUNCH_CHECK("tc_reduce_kernel");
+    tc_reduce_kernel<<<(unsigned)rtr_ceil_div(c3 * 32, 256), 256, 0, s>>>(a.part3, g.gx, c3, Y3, nullptr, 0,
+                                                                        nullptr, p->flags);
+    RTR_LAUNCH_CHECK("tc_reduce_kernel");
+    *done = 1;
+    return RTR_OK;
+}
 
 int launch_sketch_tma(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
                       double* norm_out, cudaStream_t s, int64_t aoff) {
@@ -1036,7 +1496,14 @@ int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int
 
 int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s) {
     bool norm_done = false;
-    for (int n = 0; n < p->N; ++n) {
+    // modes N-2 and N-1 in one pass when the plan asks for it (BF16, RTR_PARAM_PAIR)
+    int nmodes = p->N, pair = 0;
+    if (p->N >= 3 && p->proj[p->N - 2] && p->proj[p->N - 1]) {
+        const int st = launch_sketch_pair(p, X, Y[p->N - 2], Y[p->N - 1], p->scal + 0, s, &pair);
+        if (st) return st;
+        if (pair) { nmodes = p->N - 2; norm_done = true; }
+    }
+    for (int n = 0; n < nmodes; ++n) {
         if (!p->proj[n]) continue;
         int64_t A, I, B;
         rtr_mode_view(p->N, p->dims, n, &A, &I, &B);

@@ -260,6 +260,10 @@ int rtr_plan_create(rtr_plan** plan, int N, const int64_t* dims, const int* K, c
             normp = std::max(normp, contract_norm_elems(p->num_sms, dims[n], p->K[n]));
             maxI = std::max<int64_t>(maxI, dims[n]);
         }
+        // the BF16 sketch of the last two modes in one pass (mode N-2 partials
+        // per CTA column, mode N-1 partials per CTA)
+        if (n == N - 1 && N >= 3 && p->params.prec == RTR_BF16 && p->proj[N - 2] && p->proj[N - 1])
+            part = std::max(part, pair_partial_elems(p->num_sms, dims[N - 2], p->K[N - 2], dims[N - 1], p->K[N - 1]));
         const int C = R[n] * R[(n + 1) % N];
         part = std::max(part, contract_partial_elems(p->num_sms, p->K[n], C));
         maxJ = std::max<int64_t>(maxJ, p->pnumel / p->K[n]);
@@ -389,6 +393,12 @@ int rtr_plan_info(const rtr_plan* p, int* K_eff, int* chain_order) {
         if (K_eff) K_eff[n] = p->K[n];
         if (chain_order) chain_order[n] = p->order[n];
     }
+    return RTR_OK;
+}
+
+int rtr_plan_sketch_passes(const rtr_plan* p, int* passes) {
+    if (!p || !passes) return rtr_set_error(RTR_EINVAL, "NULL argument");
+    *passes = sketch_passes(p);
     return RTR_OK;
 }
 

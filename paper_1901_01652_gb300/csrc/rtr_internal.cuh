@@ -163,6 +163,14 @@ int batch_als_flags(BatchAls* b, int* flags);
 int launch_sketch_tc_mode(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, int n, double* Y,
                           double* norm_out, cudaStream_t s, int64_t aoff);
 int launch_sketch_tc(rtr_plan* p, const float* X, double* const* Y, cudaStream_t s);
+// modes N-2 and N-1 of the BF16 sketch in one pass over X (*done = 0: not taken)
+int launch_sketch_pair(rtr_plan* p, const float* X, double* Y2, double* Y3, double* norm_out, cudaStream_t s,
+                       int* done);
+// partial-sum elements that pass needs (at most)
+size_t pair_partial_elems(int num_sms, int64_t I, int K2, int64_t J, int K3);
+// reads of a 16-byte aligned X by rtr_sketch (one per projected mode, one
+// less when the last two modes share a pass: RTR_PARAM_PAIR)
+int sketch_passes(const rtr_plan* p);
 int launch_ttm_tc(rtr_plan* p, const float* X, int64_t A, int64_t I, int64_t B, const double* Q, int K, float* out,
                   cudaStream_t s);
 

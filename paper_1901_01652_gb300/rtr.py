@@ -18,12 +18,12 @@ RTR_OK, RTR_EINVAL, RTR_ENOMEM, RTR_ECUDA, RTR_ENONFINITE, RTR_ENOTCONV, RTR_ETI
 RTR_FP64, RTR_FP32, RTR_BF16, RTR_FP8 = 0, 1, 2, 3
 PREC = {"fp64": RTR_FP64, "fp32": RTR_FP32, "bf16": RTR_BF16, "fp8": RTR_FP8}
 FLAG_NONFINITE, FLAG_QR_FALLBACK, FLAG_GRAM_PINV, FLAG_TIMEOUT = 1, 2, 4, 8
-PARAM_NO_GRAPH = 1
+PARAM_NO_GRAPH, PARAM_PAIR = 1, 2
 
 # every entry point of include/rtr.h
 ENTRY_POINTS = (
     "rtr_params_default", "rtr_last_error", "rtr_kernel_launches", "rtr_plan_create", "rtr_plan_destroy", "rtr_plan_info",
-    "rtr_plan_flags", "rtr_sketch", "rtr_project", "rtr_project_sequential", "rtr_project_host", "rtr_als", "rtr_svd", "rtr_backproject",
+    "rtr_plan_flags", "rtr_plan_sketch_passes", "rtr_sketch", "rtr_project", "rtr_project_sequential", "rtr_project_host", "rtr_als", "rtr_svd", "rtr_backproject",
     "rtr_reconstruct_work_bytes", "rtr_reconstruct", "rtr_rse", "rtr_draw_omega", "rtr_gaussian_table",
     "rtr_sketch_mode_noalloc", "rtr_batch_create", "rtr_batch_destroy", "rtr_batch_run",
     "rtr_batch_graph_kernels", "rtr_batch_flags", "rtr_mlp_param_count", "rtr_mlp_work_bytes", "rtr_spectrum_features",
@@ -66,6 +66,7 @@ def lib():
         "rtr_plan_destroy": (ctypes.c_int, [_VP]),
         "rtr_plan_info": (ctypes.c_int, [_VP, _IP, _IP]),
         "rtr_plan_flags": (ctypes.c_int, [_VP, _IP]),
+        "rtr_plan_sketch_passes": (ctypes.c_int, [_VP, _IP]),
         "rtr_sketch": (ctypes.c_int, [_VP, _VP, _VPP, _VP]),
         "rtr_project": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
         "rtr_project_sequential": (ctypes.c_int, [_VP, _VP, _VPP, _VPP, _VP, _VP]),
@@ -189,8 +190,9 @@ def rtr_params_default():
     return p
 
 
-def make_params(prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None, power=0):
+def make_params(prec="fp32", seed=0, sweeps=20, tol=1e-2, chain_order=None, power=0, flags=0):
     p = rtr_params_default()
+    p.flags = int(flags)
     p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     p.seed = int(seed)
     p.sweeps = int(sweeps)
@@ -217,6 +219,13 @@ def rtr_plan_flags(plan):
     f = ctypes.c_int(0)
     _check(lib().rtr_plan_flags(plan.handle, ctypes.byref(f)))
     return f.value
+
+
+def rtr_plan_sketch_passes(plan):
+    """Passes over X that rtr_sketch makes for this plan (16-byte aligned X)."""
+    n = ctypes.c_int(0)
+    _check(lib().rtr_plan_sketch_passes(plan.handle, ctypes.byref(n)))
+    return n.value
 
 
 def rtr_sketch(plan, X, Y, stream=None):

@@ -44,15 +44,20 @@ LAST_MODE_CASES = [
 ]
 
 
+PAIR = [pytest.param(rtr.PARAM_PAIR, id="pair"), pytest.param(0, id="per_mode")]
+
+
+@pytest.mark.parametrize("flags", PAIR)
 @pytest.mark.parametrize("dims,K", LAST_MODE_CASES)
-def test_bf16_last_mode_tma_sketch_vs_oracle(dims, K):
+def test_bf16_last_mode_tma_sketch_vs_oracle(dims, K, flags):
     """The last mode through the TMA sketch with an MN-major operand: boxes of
-    64 rows x 64 columns, zero-filled past I and past A."""
+    64 rows x 64 columns, zero-filled past I and past A (per_mode), or from the
+    tiles of the two-mode pass (pair)."""
     dims = tuple(dims)
     full = dims if len(dims) >= 3 else (1,) + dims
     Kf = K if len(K) >= 3 else (1,) + tuple(K)
     X32 = np.random.default_rng(25).standard_normal(full).astype(np.float32)
-    plan = rtr.rtr_plan_create(full, Kf, (2,) * len(full), rtr.make_params("bf16", 79))
+    plan = rtr.rtr_plan_create(full, Kf, (2,) * len(full), rtr.make_params("bf16", 79, flags=flags))
     Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") if pr else None
          for d, k, pr in zip(plan.dims, plan.K, plan.projected)]
     rtr.rtr_sketch(plan, torch.from_numpy(X32).cuda(), Y)
@@ -63,11 +68,12 @@ def test_bf16_last_mode_tma_sketch_vs_oracle(dims, K):
     assert rel(Y[n].cpu().numpy(), ref[n]) < 2e-5
 
 
+@pytest.mark.parametrize("flags", PAIR)
 @pytest.mark.parametrize("dims,K", TC_CASES)
-def test_bf16_sketch_vs_oracle(dims, K):
+def test_bf16_sketch_vs_oracle(dims, K, flags):
     X32 = np.random.default_rng(21).standard_normal(dims).astype(np.float32)
     plan = rtr.rtr_plan_create(dims, K, (2,) * len(dims),
-                               rtr.make_params("bf16", 77, 3, 1e-2, orc.default_chain_order(dims, K)))
+                               rtr.make_params("bf16", 77, 3, 1e-2, orc.default_chain_order(dims, K), flags=flags))
     Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") if pr else None
          for d, k, pr in zip(plan.dims, plan.K, plan.projected)]
     rtr.rtr_sketch(plan, torch.from_numpy(X32).cuda(), Y)
@@ -165,3 +171,55 @@ def test_bf16_sketch_and_chain_at_the_200x4_kernel_configurations():
     assert rtr.rtr_plan_flags(plan) == 0
     Pr = orc.project(X, [np.eye(d) if y is None else orc.orth(y) for d, y in zip(dims, Yr)], order)
     assert rel(P.cpu().numpy(), Pr) < 3e-5
+
+
+PAIR_CASES = [
+    ((7, 200, 200), (5, 25, 25)),            # I = J = 200: two i tiles and two j tiles, both ragged
+    ((3, 130, 180), (2, 40, 20)),            # second i tile 2 rows; last j tile 52 wide (one box); N = 64 / 32
+    ((2, 2, 64, 1024), (1, 1, 30, 31)),      # eight j tiles, 32 chunks: one chunk per CTA
+    ((40, 36, 44), (5, 9, 11)),              # one i tile of 36 rows, one box of 44 j
+    ((5, 4, 136, 200), (3, 3, 64, 64)),      # K = 64 for both (two X slots, 96 KB of Omega rings)
+    ((4, 300, 100), (3, 20, 12)),            # three i tiles (the mode N-1 Omega group holds 384 rows)
+    ((1000, 20, 8), (9, 7, 5)),              # many chunks per CTA, J = 8
+]
+
+
+@pytest.mark.parametrize("dims,K", PAIR_CASES)
+def test_bf16_pair_sketch_vs_oracle(dims, K):
+    """The last two modes from one pass over X (sketch_pair_kernel) against the
+    oracle, and against the per-mode passes on the GPU; the pass count says
+    which path ran."""
+    X32 = np.random.default_rng(31).standard_normal(dims).astype(np.float32)
+    Xd = torch.from_numpy(X32).cuda()
+    out = {}
+    for flags in (rtr.PARAM_PAIR, 0):
+        plan = rtr.rtr_plan_create(dims, K, (2,) * len(dims), rtr.make_params("bf16", 83, flags=flags))
+        nproj = sum(plan.projected)
+        assert rtr.rtr_plan_sketch_passes(plan) == (nproj - 1 if flags else nproj)
+        Y = [torch.zeros((d, k), dtype=torch.float64, device="cuda") if pr else None
+             for d, k, pr in zip(plan.dims, plan.K, plan.projected)]
+        rtr.rtr_sketch(plan, Xd, Y)
+        torch.cuda.synchronize()
+        assert rtr.rtr_plan_flags(plan) == 0
+        out[flags] = [y.cpu().numpy() if y is not None else None for y in Y]
+    ref = orc.sketch(X32.astype(np.float64), K, 83, "bf16")
+    for n in range(len(dims)):
+        if ref[n] is None:
+            continue
+        assert rel(out[rtr.PARAM_PAIR][n], ref[n]) < 2e-5, n
+        assert rel(out[rtr.PARAM_PAIR][n], out[0][n]) < 1e-5, n
+
+
+def test_sketch_passes_by_precision():
+    """Only BF16 plans that ask for it take the two-mode pass; FP32, FP64 and
+    FP8 plans read X once per projected mode, and so does a BF16 plan without
+    the flag or whose last mode is whole or has I_N % 4 != 0."""
+    dims, K, pair = (30, 40, 48), (10, 10, 10), rtr.PARAM_PAIR
+    for prec, flags, want in (("bf16", pair, 2), ("bf16", 0, 3), ("fp32", pair, 3), ("fp64", pair, 3),
+                              ("fp8", pair, 3)):
+        plan = rtr.rtr_plan_create(dims, K, (2, 2, 2), rtr.make_params(prec, 1, flags=flags))
+        assert rtr.rtr_plan_sketch_passes(plan) == want, (prec, flags)
+    assert rtr.rtr_plan_sketch_passes(rtr.rtr_plan_create((30, 40, 48), (10, 10, 48), (2, 2, 2),
+                                                          rtr.make_params("bf16", 1, flags=pair))) == 2
+    assert rtr.rtr_plan_sketch_passes(rtr.rtr_plan_create((30, 40, 50), (10, 10, 10), (2, 2, 2),
+                                                          rtr.make_params("bf16", 1, flags=pair))) == 3
