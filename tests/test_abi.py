@@ -135,3 +135,16 @@ def test_noalloc_wrapper_refuses_a_view_that_does_not_match_the_buffers():
         rtr.rtr_sketch_mode_noalloc("fp32", X, (1, 40000, 1), 64, 0, 0, Y)
     with pytest.raises(ValueError, match="I\\*K"):
         rtr.rtr_sketch_mode_noalloc("fp32", X, (1, 4, 1), 3, 0, 0, Y)
+
+
+def test_host_queries_reject_null_arguments(L):
+    """The host-only plan queries refuse a NULL plan or output pointer with
+    RTR_EINVAL before touching the device."""
+    from paper_1901_01652_gb300 import rtr
+    n = ctypes.c_int(-1)
+    assert L.rtr_plan_sketch_passes(None, ctypes.byref(n)) == rtr.RTR_EINVAL
+    assert n.value == -1
+    assert L.rtr_plan_info(None, None, None) == rtr.RTR_EINVAL
+    assert rtr.PARAM_PAIR == 2 and rtr.PARAM_NO_GRAPH == 1
+    assert rtr.make_params("bf16", 1, flags=rtr.PARAM_PAIR).flags == rtr.PARAM_PAIR
+    assert rtr.make_params("bf16", 1).flags == 0
