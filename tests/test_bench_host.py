@@ -98,3 +98,17 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     import bench
     assert d["metric"] == bench.METRIC
+
+
+def test_pipeline_bytes_accounting():
+    """The roofline's algorithmic bytes of the sketch-and-projection phase:
+    two reads of X (strict) or one per projected mode plus one (per-mode
+    accounting), plus each chain intermediate written and read once and P
+    written.  200^4 with K = 25 gives the 14.6 GB and 33.8 GB of the scope
+    table; the small case is counted by hand (mode 1 kept whole)."""
+    import bench
+    assert bench.pipeline_bytes((200,) * 4, (25,) * 4, [0, 1, 2, 3]) == (14626562500, 33826562500)
+    assert bench.pipeline_bytes((200,) * 4, (25,) * 4, [3, 1, 2, 0]) == (14626562500, 33826562500)
+    # (10, 20, 30), K = (5, 20, 6), order 2, 0, 1: intermediates 1200 and 600
+    # elements written and read, P = 600 elements written: 16800 B
+    assert bench.pipeline_bytes((10, 20, 30), (5, 20, 6), [2, 0, 1]) == (2 * 6000 * 4 + 16800, 3 * 6000 * 4 + 16800)
